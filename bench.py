@@ -1,0 +1,535 @@
+#!/usr/bin/env python3
+"""Throughput of the 2D/3D type 1 + type 2 NUFFT hot path on GB300.
+
+One step = the whole hot path over one batch of synthetic points: for a type 1
+plan and a type 2 plan on the same M points, setpts (bin-sort) then execute
+(spread -> cuFFT -> deconvolve, and precorrect -> cuFFT -> interpolate).
+value = nonuniform points transformed per second over both plans
+        (2 * M * ntransf per step), inputs resident in HBM, L2 flushed between steps.
+e2e   = the same through the public API with host buffers: pinned host->device
+        copies of x, y(, z), c, f and device->host copies of both results inside
+        the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                       [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the transform has no exchange step); value sums the ranks' points over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2102_08463_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "NU points/sec (spread/interp and full exec) at eps=1e-5 fp32"
+UNIT = "points/s"
+
+WORKLOADS = {
+    "2d-1024-rand-eps1e-5": dict(dim=2, N=(1024, 1024), M=4194304, eps=1e-5, prec=0, kind="rand"),
+    "2d-1024-rand-eps1e-2": dict(dim=2, N=(1024, 1024), M=4194304, eps=1e-2, prec=0, kind="rand"),
+    "2d-1024-rand-eps1e-9": dict(dim=2, N=(1024, 1024), M=4194304, eps=1e-9, prec=1, kind="rand"),
+    "2d-1024-rand-eps1e-12": dict(dim=2, N=(1024, 1024), M=4194304, eps=1e-12, prec=1, kind="rand"),
+    "3d-128-rand-eps1e-2": dict(dim=3, N=(128, 128, 128), M=16777216, eps=1e-2, prec=0, kind="rand"),
+    "3d-128-rand-eps1e-6": dict(dim=3, N=(128, 128, 128), M=16777216, eps=1e-6, prec=0, kind="rand"),
+    "3d-128-gauss-eps1e-2": dict(dim=3, N=(128, 128, 128), M=16777216, eps=1e-2, prec=0, kind="gauss"),
+    "3d-128-gauss-eps1e-6": dict(dim=3, N=(128, 128, 128), M=16777216, eps=1e-6, prec=0, kind="gauss"),
+    "2d-64-rand-eps1e-5": dict(dim=2, N=(64, 64), M=4096, eps=1e-5, prec=0, kind="rand"),
+}
+DEFAULT_WORKLOAD = "2d-1024-rand-eps1e-5"
+SEED = wl.BASE_SEED + 1
+
+# Roofline denominators.  HBM: the measured copy bandwidth of this GPU pool
+# (MEASURED_PEAKS.json), else 6800 GB/s.  FP32 / FP64 ALU: 152 SMs x 128 FP32
+# lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s; FP64 1.25 TFLOP/s (GB300 nominal).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+# DRAM traffic per launch from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by kernel and workload, with the hash of the
+# kernel sources at capture time; a stale hash reports null.
+TRAFFIC = {}
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for f in ("spread_interp.cuh", "nufft_internal.cuh", "setpts.cu", "correct.cu", "plan.cu"):
+        with open(os.path.join(ROOT, "paper_2102_08463_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    hbm, src = 6800.0, "fallback"
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as fh:
+                hbm = float(json.load(fh)["hbm_gbs"])
+            src = "measured"
+        except Exception:
+            pass
+    return hbm, src
+
+
+def algorithmic_cost(W, w, kernel):
+    """Bytes and flops per launch of one spread / interp kernel (ntransf = 1).
+
+    bytes = M (d s + 2 s) + n_tot 2 s: coordinates and strengths once, the fine
+    grid written (spread) or read (interp) once.  flops = M (8 d w + (d + 3) w^d):
+    d w kernel evaluations of 8 operations, then per window cell (d - 1) weight
+    products and a complex-by-real accumulate (4).
+    """
+    d = W["dim"]
+    s = 4 if W["prec"] == 0 else 8
+    nf = 1
+    for v in W["nf"]:
+        nf *= v
+    M = W["M"]
+    byts = M * (d * s + 2 * s) + nf * 2 * s
+    flops = M * (8 * d * w + (d + 3) * w ** d)
+    return byts, flops
+
+
+# ---------------------------------------------------------------------------
+# nvidia-smi clock sampler
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def make_inputs(W, seed):
+    dt = np.float32 if W["prec"] == 0 else np.float64
+    ct = np.complex64 if W["prec"] == 0 else np.complex128
+    pts = wl.points(W["kind"], W["dim"], W["M"], seed, dt, n=W.get("nf"))
+    c = wl.strengths(W["M"], seed + 1, ct)
+    f = wl.modes(W["N"], seed + 2, ct)
+    return pts, c, f
+
+
+def run_gpu(args, W, rank, world, local_rank):
+    import torch
+    from paper_2102_08463_gb300 import binding
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    method1 = args.method1
+    method2 = args.method2
+    p1 = binding.Plan(1, W["N"], W["eps"], prec=W["prec"], method=method1, stream=stream)
+    p2 = binding.Plan(2, W["N"], W["eps"], prec=W["prec"], method=method2, stream=stream)
+    W["nf"] = p1.params["nf"][: W["dim"]]
+    w = p1.params["w"]
+    pts, c, f = make_inputs(W, SEED + 17 * rank)
+    rd = p1.real_dtype
+    cd = p1.complex_dtype
+    dpts = [torch.from_numpy(p).to(dev) for p in pts]
+    dc = torch.from_numpy(c).to(dev)
+    df = torch.from_numpy(f).to(dev)
+    fout = torch.empty(tuple(reversed(W["N"])), dtype=cd, device=dev)
+    cout = torch.empty(W["M"], dtype=cd, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        p1.setpts(*dpts)
+        p1.execute(c=dc, f=fout)
+        p2.setpts(*dpts)
+        p2.execute(f=df, c=cout)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, CUDA events on the stream ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = binding.get_launch_count()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = binding.get_launch_count() - launches0
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    total_ms = float(t_max.item())
+    ms_per_step = total_ms / args.steps
+    units = 2 * W["M"] * world
+    value = units / (ms_per_step / 1e3)
+
+    # ---- stage breakdown and the kernels' own durations (outside the timed region) ----
+    def timed(fn, reps=args.stage_reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    h1, h2 = p1.handle, p2.handle
+    dcp = binding._dptr(dc)
+    dfp = binding._dptr(df)
+    fop = binding._dptr(fout)
+    cop = binding._dptr(cout)
+    stages = {
+        "setpts_ms": timed(lambda: p1.setpts(*dpts)),
+        "spread_ms": timed(lambda: binding.spread_add(h1, dcp)),
+        "spread_with_clear_ms": timed(lambda: binding.spread(h1, dcp)),
+        "fft_ms": timed(lambda: binding.fft(h1)),
+        "deconvolve_ms": timed(lambda: binding.deconvolve(h1, fop)),
+        "precorrect_ms": timed(lambda: binding.precorrect(h2, dfp)),
+        "interp_ms": timed(lambda: binding.interp(h2, cop)),
+        "exec_type1_ms": timed(lambda: binding.execute(h1, dcp, fop)),
+        "exec_type2_ms": timed(lambda: binding.execute(h2, cop, dfp)),
+    }
+    # restore correct outputs for the accuracy check
+    step()
+    torch.cuda.synchronize()
+
+    # ---- roofline of the dominant kernel ----
+    hbm, hbm_src = _peaks()
+    byts, flops = algorithmic_cost(W, w, "spread")
+    fp_peak = FP32_PEAK_TFLOPS if W["prec"] == 0 else FP64_PEAK_TFLOPS
+    roof = {}
+    for name, key in (("spread", "spread_ms"), ("interp", "interp_ms")):
+        t = stages[key] / 1e3
+        t_hbm = byts / (hbm * 1e9)
+        t_alu = flops / (fp_peak * 1e12)
+        if t_hbm >= t_alu:
+            ach = byts / t / 1e9
+            roof[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                          "frac": round(ach / hbm, 4), "peak_source": hbm_src}
+        else:
+            ach = flops / t / 1e12
+            roof[name] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp_peak, 2),
+                          "unit": "TFLOP/s", "frac": round(ach / fp_peak, 4),
+                          "peak_source": "derived: SM count x lanes x 2 x max clock"}
+        roof[name]["algorithmic_bytes"] = byts
+        roof[name]["algorithmic_flops"] = flops
+        roof[name]["kernel_ms"] = round(stages[key], 5)
+    dom = "spread" if stages["spread_ms"] >= stages["interp_ms"] else "interp"
+    roofline = dict(roof[dom])
+    roofline["kernel"] = dom
+    tkey = "%s:%s:%s" % (dom, args.workload, _src_hash())
+    roofline["traffic"] = TRAFFIC.get(tkey)
+
+    # ---- end to end through the public API with host buffers ----
+    hpts = [torch.from_numpy(p).pin_memory() for p in pts]
+    hc = torch.from_numpy(c).pin_memory()
+    hf = torch.from_numpy(f).pin_memory()
+    hfo = torch.empty(fout.shape, dtype=cd).pin_memory()
+    hco = torch.empty(cout.shape, dtype=cd).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hpts) + hc.numel() * hc.element_size() \
+        + hf.numel() * hf.element_size()
+    d2h = hfo.numel() * hfo.element_size() + hco.numel() * hco.element_size()
+
+    def e2e_step():
+        for hsrc, ddst in zip(hpts, dpts):
+            ddst.copy_(hsrc, non_blocking=True)
+        dc.copy_(hc, non_blocking=True)
+        df.copy_(hf, non_blocking=True)
+        step()
+        hfo.copy_(fout, non_blocking=True)
+        hco.copy_(cout, non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize()
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ee[i][0].record(stream)
+        e2e_step()
+        ee[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ee) / args.steps
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(e2e_t.item())
+
+    # ---- accuracy against the FP64 oracle on sampled modes / targets ----
+    acc = None
+    if rank == 0 and not args.no_accuracy:
+        acc = sampled_accuracy(W, pts, c, f, hfo.numpy(), hco.numpy())
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if W["prec"] == 0 else "f64",
+        "data": "synthetic (seeded SplitMix64: %s points, N(0,1) strengths and modes)" % W["kind"],
+        "config": {"workload": "%s: %dD type 1 + type 2, N=%s, fine grid %s, M=%d, eps=%g, %s"
+                               % (args.workload, W["dim"], "x".join(map(str, W["N"])),
+                                  "x".join(map(str, W["nf"])), W["M"], W["eps"],
+                                  "complex64" if W["prec"] == 0 else "complex128"),
+                   "methods": {"type1": p1.params["method"], "type2": p2.params["method"]},
+                   "kernel_width": w, "ntransf": 1,
+                   "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "roofline_kernels": roof,
+        "stages_ms": {k: round(v, 5) for k, v in stages.items()},
+        "pts_per_s": {
+            "spread": round(W["M"] / (stages["spread_ms"] / 1e3), 1),
+            "interp": round(W["M"] / (stages["interp_ms"] / 1e3), 1),
+            "exec_type1": round(W["M"] / (stages["exec_type1_ms"] / 1e3), 1),
+            "exec_type2": round(W["M"] / (stages["exec_type2_ms"] / 1e3), 1),
+        },
+        "e2e": {"value": round(units / (e2e_ms / 1e3), 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": round(e2e_ms, 5)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if acc is not None:
+        out["rel_l2_vs_oracle_sampled"] = acc
+    p1.close()
+    p2.close()
+    return out
+
+
+def sampled_accuracy(W, pts, c, f, f_gpu, c_gpu, nsamp=48):
+    """Relative l2 error of the GPU outputs on sampled modes / targets (exact sums)."""
+    import oracle
+    p64 = [p.astype(np.float64) for p in pts]
+    Ntot = int(np.prod(W["N"]))
+    kidx = wl.sample_indices(Ntot, nsamp, SEED + 5)
+    jidx = wl.sample_indices(W["M"], nsamp, SEED + 6)
+    f_ref = oracle.direct_type1(p64, c.astype(np.complex128), W["N"], +1, modes=kidx)
+    c_ref = oracle.direct_type2(p64, f.astype(np.complex128), +1, targets=jidx)
+    return {"type1": oracle.rel_l2(f_gpu.ravel()[kidx], f_ref),
+            "type2": oracle.rel_l2(c_gpu.ravel()[jidx], c_ref),
+            "samples": nsamp, "reference": "FP64 exact sums (oracle O1)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arm
+# ---------------------------------------------------------------------------
+def oracle_step(W, pts, c, f):
+    import oracle
+    p64 = [p.astype(np.float64) for p in pts]
+    oracle.nufft_type1(p64, c.astype(np.complex128), W["N"], eps=W["eps"])
+    oracle.nufft_type2(p64, f.astype(np.complex128), eps=W["eps"])
+
+
+def cpu_sample(W, budget_s):
+    """Pick a point count for one oracle step of about budget_s seconds."""
+    import oracle
+    if "nf" not in W:
+        P = oracle.Params(W["N"], W["eps"])
+        W["nf"] = P.n
+    m0 = min(W["M"], 65536)
+    Ws = dict(W, M=m0)
+    pts, c, f = make_inputs(Ws, SEED)
+    t0 = time.perf_counter()
+    oracle_step(Ws, pts, c, f)
+    t_small = time.perf_counter() - t0
+    Ws = dict(W, M=min(W["M"], 4 * m0))
+    pts, c, f = make_inputs(Ws, SEED)
+    t0 = time.perf_counter()
+    oracle_step(Ws, pts, c, f)
+    t_big = time.perf_counter() - t0
+    per_pt = max((t_big - t_small) / max(Ws["M"] - m0, 1), 1e-9)
+    fixed = max(t_small - per_pt * m0, 0.0)
+    m = int(max(m0, min(W["M"], (budget_s - fixed) / per_pt)))
+    return m
+
+
+def run_cpu_baseline(W, budget_s=15.0, steps=1):
+    import oracle
+    oracle.set_num_threads(os.cpu_count() or 1)
+    cores = oracle.num_threads()
+    m = cpu_sample(W, budget_s / max(steps, 1))
+    Ws = dict(W, M=m)
+    pts, c, f = make_inputs(Ws, SEED)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle_step(Ws, pts, c, f)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": round(2 * m / dt, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one type 1 + type 2 FP64 oracle pipeline step (C spread/interp with "
+                      "OpenMP, numpy FFT) on %d of the %d points, full %s fine grid, eps=%g"
+                      % (m, W["M"], "x".join(map(str, W["nf"])), W["eps"]),
+            "s_per_step": round(dt, 3)}
+
+
+def run_reference(args, W, rank):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    oracle.set_num_threads(os.cpu_count() or 1)
+    cores = oracle.num_threads()
+    per_step_budget = max(0.5, 150.0 / max(args.steps + args.warmup, 1))
+    m = cpu_sample(W, per_step_budget)
+    Ws = dict(W, M=m)
+    pts, c, f = make_inputs(Ws, SEED)
+    for _ in range(args.warmup):
+        oracle_step(Ws, pts, c, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(Ws, pts, c, f)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 2 * m / dt
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64), bounded sample of the workload",
+        "config": {"workload": "%s: %dD type 1 + type 2, N=%s, M=%d (sample %d), eps=%g"
+                               % (args.workload, W["dim"], "x".join(map(str, W["N"])), W["M"],
+                                  m, W["eps"])},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d of %d points per step, full fine grid" % (m, W["M"])},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--method1", default="auto")
+    ap.add_argument("--method2", default="auto")
+    ap.add_argument("--stage-reps", type=int, default=10)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the sampled accuracy check")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    W = dict(WORKLOADS[args.workload])
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        out = run_reference(args, W, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_gpu(args, W, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = run_cpu_baseline(W)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

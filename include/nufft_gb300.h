@@ -1,0 +1,159 @@
+/*
+ * nufft_gb300.h -- C ABI of the GB300 (sm_103a) nonuniform FFT library.
+ *
+ * Computes the 2D and 3D type 1 and type 2 NUFFT of Shih et al., "cuFINUFFT:
+ * a load-balanced GPU library for general-purpose nonuniform FFTs"
+ * (arXiv 2102.08463), with the paper's "plan, setup, execute, destroy"
+ * interface (Sec. 1.1).
+ *
+ *   type 1 (Eq. 2d1):  f_k = sum_{j<M} c_j exp( i*iflag*(k . x_j) ),   k in I_N1 x I_N2 (x I_N3)
+ *   type 2 (Eq. 2d2):  c_j = sum_k    f_k exp(-i*iflag*(k . x_j) ),   j < M
+ *
+ * with I_N = { -floor(N/2), ..., ceil(N/2)-1 } (Eq. I).  The paper writes type 1
+ * with exponent -i and type 2 with +i; that is iflag = -1 here.  The result is
+ * approximated to a relative l2 tolerance near eps by the three-step algorithm
+ * of Sec. 3 (spread / FFT / correct, and its transpose).
+ *
+ * Memory layout and ownership
+ *   - All array arguments are DEVICE pointers on the current CUDA device, in
+ *     the plan's precision (prec 0: float / interleaved complex float,
+ *     prec 1: double / interleaved complex double).
+ *   - Nonuniform points: three separate arrays x, y, z of M reals (z is NULL
+ *     in 2D).  Coordinates are periodic with period 2 pi; accuracy is as stated
+ *     for x in [-3 pi, 3 pi); values beyond +-1024 are clamped.
+ *   - Strengths / targets c: ntransf vectors of M complex values, c[t*M + j].
+ *   - Modes f: ntransf arrays of N1*N2(*N3) complex values, f[t][k3][k2][k1],
+ *     k1 fastest, each axis ordered from -floor(N_i/2) upwards.
+ *   - The plan owns every buffer it allocates (fine grid, sort arrays, cuFFT
+ *     plan).  setpts copies what it needs: the caller may free x, y, z after
+ *     setpts returns and the stream has passed it.
+ *   - Calls are asynchronous on opts.stream; they enqueue work and return.
+ *
+ * Errors: every function returns 0 on success or a negative NUFFT_ERR_* code;
+ * none aborts, traps or prints.  After any error the plan can still be passed
+ * to nufft_destroy.
+ */
+#ifndef NUFFT_GB300_H
+#define NUFFT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define NUFFT_OK               0
+#define NUFFT_ERR_ARG         -1   /* invalid argument (type, dim, sizes, null pointer, option) */
+#define NUFFT_ERR_EPS         -2   /* tolerance outside the supported range for the precision */
+#define NUFFT_ERR_SIZE        -3   /* mode count or fine grid too large */
+#define NUFFT_ERR_ALLOC       -4   /* device allocation failed */
+#define NUFFT_ERR_CUDA        -5   /* CUDA runtime error while enqueueing work */
+#define NUFFT_ERR_CUFFT       -6   /* cuFFT plan or execution error */
+#define NUFFT_ERR_NOPTS       -7   /* execute before setpts */
+#define NUFFT_ERR_TIMEOUT     -8   /* a bounded device wait gave up (batched launch) */
+#define NUFFT_ERR_METHOD      -9   /* requested method not available for this plan */
+
+/* Spreading / interpolation methods (Sec. 4.1, 4.2). */
+#define NUFFT_METHOD_AUTO      0   /* the library's heuristic */
+#define NUFFT_METHOD_GM        1   /* one thread group per point, user order, global atomics */
+#define NUFFT_METHOD_GM_SORT   2   /* the same in bin-sorted order */
+#define NUFFT_METHOD_SM        3   /* type 1: shared-memory subproblems (Sec. 4.1 SM);
+                                      type 2: padded bin staged in shared memory, sorted gather */
+
+typedef struct nufft_plan_s *nufft_plan;   /* opaque, library-owned */
+
+typedef struct {
+    int    method;        /* NUFFT_METHOD_*; 0 = auto */
+    int    bin[3];        /* bin size m_i in fine-grid cells; 0 = default (32x32, 16x16x2, Sec. 4.1 remark) */
+    int    msub;          /* max points per subproblem M_sub; 0 = default 1024 (Sec. 4.1 remark) */
+    double upsampfac;     /* sigma; 0 or 2.0 = the paper's 2; 1.25 = the lower-memory variant */
+    void  *stream;        /* cudaStream_t to enqueue on; NULL = legacy default stream */
+    int    threads;       /* threads per block for spread / interp; 0 = default 256 */
+    int    ctas_per_sm;   /* persistent CTAs per SM for the subproblem kernels; 0 = auto */
+} nufft_opts;
+
+/* Fill opts with the defaults listed above. */
+void nufft_default_opts(nufft_opts *opts);
+
+/*
+ * Create a plan (Sec. 1.1 "plan"; parameters of Sec. 3).
+ *   type    1 or 2.
+ *   dim     2 or 3.
+ *   nmodes  dim entries N1, N2 (, N3), each >= 1.
+ *   iflag   +1 or -1: sign of the type 1 exponent (type 2 uses the opposite).
+ *   ntransf number of strength / coefficient vectors per execute (>= 1).
+ *   eps     requested relative tolerance; kernel width w = ceil(log10(1/eps)) + 1
+ *           (clamped to [2, 16]), beta = 2.30 w, fine grid n_i = smallest
+ *           2^a 3^b 5^c >= max(sigma N_i, 2w).
+ *   prec    0 = single, 1 = double, -1 = by tolerance (single if eps >= 1e-6).
+ *           Single precision requires eps >= 1e-6 (NUFFT_ERR_EPS otherwise).
+ *   opts    NULL for defaults.
+ *   out     receives the plan handle (NULL on failure).
+ * Allocates the fine grid (ntransf * n1*n2(*n3) complex), the correction factors
+ * and the cuFFT plan on the current device.
+ */
+int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntransf,
+                   double eps, int prec, const nufft_opts *opts, nufft_plan *out);
+
+/*
+ * Set the nonuniform points (Sec. 1.1 "setup"; bin-sort of Sec. 4.1).
+ * Computes each point's fine-grid cell, bins of m1 x m2 (x m3) cells with x
+ * fastest, the permutation t listing points bin by bin (stable: increasing
+ * original index within a bin), the subproblem list (runs of at most M_sub
+ * points of one bin) and a packed, bin-ordered copy of the kernel offsets.
+ * M = 0 is allowed.  x, y, z: device arrays of M reals (z NULL in 2D).
+ */
+int nufft_setpts(nufft_plan plan, int64_t M, const void *x, const void *y, const void *z);
+
+/*
+ * Execute (Sec. 1.1 "execute"; Sec. 3.1 for type 1, Sec. 3.2 for type 2).
+ *   type 1: reads c (ntransf*M complex), overwrites f (ntransf*N complex).
+ *   type 2: reads f, overwrites c.
+ */
+int nufft_execute(nufft_plan plan, void *c, void *f);
+
+/* Free everything the plan owns (Sec. 1.1 "destroy").  NULL is accepted. */
+int nufft_destroy(nufft_plan plan);
+
+/* Static message for an error code. */
+const char *nufft_strerror(int code);
+
+/* ---- stage entry points (the same kernels execute runs, one step at a time) ---- */
+
+/* Type 1 step 1 (Sec. 3.1): zero the fine grid and spread c into it. */
+int nufft_spread(nufft_plan plan, const void *c);
+/* The spreading kernel alone: adds the spread of c into the fine grid as it is. */
+int nufft_spread_add(nufft_plan plan, const void *c);
+/* Type 2 step 3 (Sec. 3.2): interpolate the fine grid at the points into c. */
+int nufft_interp(nufft_plan plan, void *c);
+/* Step 2 of either type: in-place cuFFT of the fine grid, direction from type and iflag. */
+int nufft_fft(nufft_plan plan);
+/* Type 1 step 3: truncate the transformed fine grid to the N modes and scale by p_k into f. */
+int nufft_deconvolve(nufft_plan plan, void *f);
+/* Type 2 step 1: scale f by p_k and zero-pad into the fine grid. */
+int nufft_precorrect(nufft_plan plan, const void *f);
+
+/* ---- introspection, for tests and benchmarks ---- */
+
+/* Kernel width, beta, fine grid sizes (3 entries, 1 for unused axes), bin sizes
+   (3 entries), number of bins, precision (0/1) and method actually used. */
+int nufft_get_params(nufft_plan plan, int *w, double *beta, int64_t *nf, int *bins,
+                     int64_t *nbins, int *prec, int *method);
+/* Device pointer and byte size of the fine grid (ntransf * n complex). */
+int nufft_get_finegrid(nufft_plan plan, void **dptr, size_t *bytes);
+/* Copy (device to device, on the plan stream) the permutation t (int32[M]),
+   the per-bin counts (int32[nbins]) and the subproblem count (int32[1]);
+   any destination may be NULL. */
+int nufft_get_sort(nufft_plan plan, int32_t *t, int32_t *bincounts, int32_t *nsub);
+
+/* Number of CUDA kernels this library has launched in this process (all plans,
+   all threads).  cuFFT's own kernels are not counted. */
+uint64_t nufft_get_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUFFT_GB300_H */

@@ -1,0 +1,338 @@
+"""Thin ctypes binding over the C ABI in include/nufft_gb300.h.
+
+Argument marshalling only: every step of the transform runs in the CUDA
+library.  Arrays are torch CUDA tensors (PyTorch provides device memory and the
+stream); the functions take their raw device pointers.  If the compiled
+library is missing this module raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB
+
+NUFFT_OK = 0
+NUFFT_ERR_ARG = -1
+NUFFT_ERR_EPS = -2
+NUFFT_ERR_SIZE = -3
+NUFFT_ERR_ALLOC = -4
+NUFFT_ERR_CUDA = -5
+NUFFT_ERR_CUFFT = -6
+NUFFT_ERR_NOPTS = -7
+NUFFT_ERR_TIMEOUT = -8
+NUFFT_ERR_METHOD = -9
+
+METHOD_AUTO, METHOD_GM, METHOD_GM_SORT, METHOD_SM = 0, 1, 2, 3
+METHODS = {"auto": 0, "gm": 1, "gmsort": 2, "sm": 3}
+
+# symbols declared in include/nufft_gb300.h
+EXPORTS = (
+    "nufft_default_opts", "nufft_makeplan", "nufft_setpts", "nufft_execute", "nufft_destroy",
+    "nufft_strerror", "nufft_spread", "nufft_interp", "nufft_fft", "nufft_deconvolve",
+    "nufft_precorrect", "nufft_get_params", "nufft_get_finegrid", "nufft_get_sort",
+    "nufft_spread_add", "nufft_get_launch_count",
+)
+
+
+class NufftError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, strerror(code), code))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int),
+        ("bin", ctypes.c_int * 3),
+        ("msub", ctypes.c_int),
+        ("upsampfac", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("threads", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return LIB
+
+
+def load():
+    """Load libnufft_gb300.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB):
+            raise ImportError("libnufft_gb300.so is not built (run __graft_entry__.build() "
+                              "or python -m paper_2102_08463_gb300.build): %s" % LIB)
+        lib = ctypes.CDLL(LIB)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        I64 = ctypes.c_int64
+        lib.nufft_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        lib.nufft_default_opts.restype = None
+        lib.nufft_makeplan.argtypes = [I, I, ctypes.POINTER(I64), I, I, ctypes.c_double, I,
+                                       ctypes.POINTER(Opts), ctypes.POINTER(P)]
+        lib.nufft_setpts.argtypes = [P, I64, P, P, P]
+        lib.nufft_execute.argtypes = [P, P, P]
+        lib.nufft_destroy.argtypes = [P]
+        lib.nufft_strerror.argtypes = [I]
+        lib.nufft_strerror.restype = ctypes.c_char_p
+        lib.nufft_spread.argtypes = [P, P]
+        lib.nufft_interp.argtypes = [P, P]
+        lib.nufft_fft.argtypes = [P]
+        lib.nufft_deconvolve.argtypes = [P, P]
+        lib.nufft_precorrect.argtypes = [P, P]
+        lib.nufft_get_params.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(I64), ctypes.POINTER(I),
+                                         ctypes.POINTER(I64), ctypes.POINTER(I),
+                                         ctypes.POINTER(I)]
+        lib.nufft_get_finegrid.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_size_t)]
+        lib.nufft_get_sort.argtypes = [P, P, P, P]
+        lib.nufft_spread_add.argtypes = [P, P]
+        lib.nufft_get_launch_count.argtypes = []
+        for name in EXPORTS:
+            if name not in ("nufft_default_opts", "nufft_strerror", "nufft_get_launch_count"):
+                getattr(lib, name).restype = I
+        lib.nufft_get_launch_count.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().nufft_strerror(int(code)).decode()
+    except ImportError:
+        return "error %d" % code
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load().nufft_default_opts(ctypes.byref(o))
+    return o
+
+
+def _check(rc, where):
+    if rc != NUFFT_OK:
+        raise NufftError(rc, where)
+
+
+def _dptr(t, dtype=None, what="array"):
+    """Raw device pointer of a contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s has dtype %s, expected %s" % (what, t.dtype, dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def makeplan(type_, dim, nmodes, iflag=+1, ntransf=1, eps=1e-6, prec=-1, opts=None):
+    """nufft_makeplan; returns the opaque handle (int)."""
+    lib = load()
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in nmodes] + [1] * (3 - len(nmodes))))
+    h = ctypes.c_void_p()
+    rc = lib.nufft_makeplan(int(type_), int(dim), arr, int(iflag), int(ntransf), float(eps),
+                            int(prec), ctypes.byref(opts) if opts is not None else None,
+                            ctypes.byref(h))
+    _check(rc, "nufft_makeplan")
+    return h.value
+
+
+def setpts(h, M, x, y, z=None):
+    _check(load().nufft_setpts(ctypes.c_void_p(h), int(M), x, y, z), "nufft_setpts")
+
+
+def execute(h, c, f):
+    _check(load().nufft_execute(ctypes.c_void_p(h), c, f), "nufft_execute")
+
+
+def destroy(h):
+    if h:
+        _check(load().nufft_destroy(ctypes.c_void_p(h)), "nufft_destroy")
+
+
+def spread(h, c):
+    _check(load().nufft_spread(ctypes.c_void_p(h), c), "nufft_spread")
+
+
+def spread_add(h, c):
+    _check(load().nufft_spread_add(ctypes.c_void_p(h), c), "nufft_spread_add")
+
+
+def get_launch_count() -> int:
+    return int(load().nufft_get_launch_count())
+
+
+def interp(h, c):
+    _check(load().nufft_interp(ctypes.c_void_p(h), c), "nufft_interp")
+
+
+def fft(h):
+    _check(load().nufft_fft(ctypes.c_void_p(h)), "nufft_fft")
+
+
+def deconvolve(h, f):
+    _check(load().nufft_deconvolve(ctypes.c_void_p(h), f), "nufft_deconvolve")
+
+
+def precorrect(h, f):
+    _check(load().nufft_precorrect(ctypes.c_void_p(h), f), "nufft_precorrect")
+
+
+def get_params(h):
+    w = ctypes.c_int()
+    beta = ctypes.c_double()
+    nf = (ctypes.c_int64 * 3)()
+    bins = (ctypes.c_int * 3)()
+    nbins = ctypes.c_int64()
+    prec = ctypes.c_int()
+    method = ctypes.c_int()
+    _check(load().nufft_get_params(ctypes.c_void_p(h), ctypes.byref(w), ctypes.byref(beta), nf,
+                                   bins, ctypes.byref(nbins), ctypes.byref(prec),
+                                   ctypes.byref(method)), "nufft_get_params")
+    return dict(w=w.value, beta=beta.value, nf=tuple(nf), bins=tuple(bins), nbins=nbins.value,
+                prec=prec.value, method=method.value)
+
+
+def get_finegrid(h):
+    p = ctypes.c_void_p()
+    n = ctypes.c_size_t()
+    _check(load().nufft_get_finegrid(ctypes.c_void_p(h), ctypes.byref(p), ctypes.byref(n)),
+           "nufft_get_finegrid")
+    return p.value, n.value
+
+
+def get_sort(h, t=None, bincounts=None, nsub=None):
+    _check(load().nufft_get_sort(ctypes.c_void_p(h), t, bincounts, nsub), "nufft_get_sort")
+
+
+# ---------------------------------------------------------------------------
+# Convenience object over the handle, on torch tensors.
+# ---------------------------------------------------------------------------
+class Plan:
+    """A plan bound to torch's current CUDA stream (or an explicit one).
+
+    Plan(type, N, eps, iflag=+1, ntransf=1, prec=-1, method="auto", ...)
+    N is (N1, N2) or (N1, N2, N3).  Arrays: x, y, z real tensors of the plan
+    precision; c complex (ntransf, M) / (M,); f complex ([ntransf,] N3, N2, N1).
+    """
+
+    def __init__(self, type_, N, eps, iflag=+1, ntransf=1, prec=-1, method="auto",
+                 bins=None, msub=0, upsampfac=2.0, stream=None, threads=0, ctas_per_sm=0):
+        import torch
+        self._torch = torch
+        self.type = int(type_)
+        self.N = tuple(int(v) for v in N)
+        self.dim = len(self.N)
+        self.ntransf = int(ntransf)
+        o = default_opts()
+        o.method = METHODS[method] if isinstance(method, str) else int(method)
+        if bins:
+            for i, b in enumerate(bins):
+                o.bin[i] = int(b)
+        o.msub = int(msub)
+        o.upsampfac = float(upsampfac)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o.stream = ctypes.c_void_p(stream.cuda_stream)
+        o.threads = int(threads)
+        o.ctas_per_sm = int(ctas_per_sm)
+        self.handle = None
+        self.handle = makeplan(self.type, self.dim, self.N, iflag, ntransf, eps, prec, o)
+        self.params = get_params(self.handle)
+        self.real_dtype = torch.float32 if self.params["prec"] == 0 else torch.float64
+        self.complex_dtype = torch.complex64 if self.params["prec"] == 0 else torch.complex128
+        self.M = 0
+        self._pts = None
+
+    def setpts(self, x, y, z=None):
+        M = x.shape[0]
+        rd = self.real_dtype
+        setpts(self.handle, M, _dptr(x, rd, "x"), _dptr(y, rd, "y"),
+               _dptr(z, rd, "z") if self.dim == 3 else None)
+        self.M = M
+        self._pts = (x, y, z)   # keep alive until the stream has consumed them
+
+    def execute(self, c=None, f=None):
+        """Type 1: c -> new f (or into f).  Type 2: f -> new c (or into c)."""
+        torch = self._torch
+        cd = self.complex_dtype
+        shp_f = tuple(reversed(self.N))
+        shp_c = (self.M,)
+        if self.ntransf > 1:
+            shp_f = (self.ntransf,) + shp_f
+            shp_c = (self.ntransf,) + shp_c
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if self.type == 1:
+            if f is None:
+                f = torch.empty(shp_f, dtype=cd, device=dev)
+            execute(self.handle, _dptr(c, cd, "c"), _dptr(f, cd, "f"))
+            return f
+        if c is None:
+            c = torch.empty(shp_c, dtype=cd, device=dev)
+        execute(self.handle, _dptr(c, cd, "c"), _dptr(f, cd, "f"))
+        return c
+
+    def finegrid(self):
+        """Copy of the plan's fine grid as a complex tensor ([ntransf,] n3, n2, n1).
+
+        Synchronises the plan's stream first (a test and diagnostics helper).
+        """
+        torch = self._torch
+        ptr, nbytes = get_finegrid(self.handle)
+        nf = self.params["nf"][: self.dim]
+        shape = tuple(reversed(nf))
+        if self.ntransf > 1:
+            shape = (self.ntransf,) + shape
+        self.stream.synchronize()
+        view = _DeviceView(ptr, shape, "<c8" if self.params["prec"] == 0 else "<c16")
+        return torch.as_tensor(view, device="cuda").clone()
+
+    def sort(self):
+        torch = self._torch
+        t = torch.empty(max(self.M, 1), dtype=torch.int32, device="cuda")
+        bc = torch.empty(self.params["nbins"], dtype=torch.int32, device="cuda")
+        ns = torch.empty(1, dtype=torch.int32, device="cuda")
+        get_sort(self.handle, _dptr(t), _dptr(bc), _dptr(ns))
+        return t[: self.M], bc, int(ns.item())
+
+    def close(self):
+        if self.handle:
+            destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class _DeviceView:
+    """Minimal __cuda_array_interface__ exporter for a library-owned buffer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {
+            "shape": tuple(int(v) for v in shape),
+            "typestr": typestr,
+            "data": (int(ptr), False),
+            "version": 3,
+            "strides": None,
+        }

@@ -1,0 +1,196 @@
+// nufft_internal.cuh -- plan object and device helpers shared by the library's
+// translation units.  See include/nufft_gb300.h for the public contract.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/nufft_gb300.h"
+
+namespace nufft {
+
+constexpr int kMaxW = 16;
+
+// Process-wide count of kernel launches made by this library.
+extern std::atomic<unsigned long long> g_launch_count;
+inline void count_launch(unsigned n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
+constexpr int kDefaultThreads = 256;
+
+// Complex storage types matching cuFFT's interleaved layout.
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+
+// Packed per-point record in bin order: kernel offsets delta_i = u_i - l0_i
+// (u_i the fine-grid coordinate, l0_i the first window cell) and the window
+// start relative to the padded bin, three 10-bit fields in one 32-bit word
+// stored in the last slot.
+template <typename T> struct rec4;
+template <> struct rec4<float> { using type = float4; };
+template <> struct rec4<double> { using type = double4; };
+
+struct Plan;
+
+// ---------------------------------------------------------------------------
+// Position rule shared by setpts and the unsorted (GM) kernels.
+//
+// A coordinate x is turned into a 64-bit fraction Phi of the period,
+// Phi / 2^64 = (x + pi) / (2 pi) mod 1, in exact integer arithmetic:
+//   X   = round-half-even(clamp(x, -1024, 1024) * 2^52)
+//   Q   = floor(|X| * K / 2^64) mod 2^64, K = round(2^76 / (2 pi))
+//   Phi = 2^63 + sign(X) Q mod 2^64
+// and along an axis with n cells: cell l = floor(Phi n / 2^64), fraction
+// F = Phi n mod 2^64.  Integer-only, so the bin of every point is the same on
+// any machine (the paper's floor((x+pi)/h), Sec. 4.1, with the rounding fixed).
+// ---------------------------------------------------------------------------
+constexpr uint64_t kKHi = 651ULL;
+constexpr uint64_t kKLo = 0xe60db9391054a7f1ULL;
+
+__device__ __forceinline__ long long coord_fixed(float x)
+{
+    float xc = x;
+    if (!(xc >= -1024.0f)) xc = -1024.0f;
+    if (xc > 1024.0f) xc = 1024.0f;
+    return __float2ll_rn(xc * 0x1p52f);        // exact scaling, then round-half-even
+}
+__device__ __forceinline__ long long coord_fixed(double x)
+{
+    double xc = x;
+    if (!(xc >= -1024.0)) xc = -1024.0;
+    if (xc > 1024.0) xc = 1024.0;
+    return __double2ll_rn(xc * 0x1p52);
+}
+
+__device__ __forceinline__ uint64_t period_fraction_fx(long long X)
+{
+    uint64_t A = X < 0 ? (uint64_t)(-X) : (uint64_t)X;
+    uint64_t Q = A * kKHi + __umul64hi(A, kKLo);
+    return (1ULL << 63) + (X < 0 ? (0ULL - Q) : Q);
+}
+
+template <typename T>
+__device__ __forceinline__ uint64_t period_fraction(T x)
+{
+    return period_fraction_fx(coord_fixed(x));
+}
+
+// Cell, window start and kernel offset along one axis.
+//   l     = floor(u), u the fine-grid coordinate (Sec. 4.1 bin rule)
+//   l0    = ceil(u - w/2), first of the w window cells (unwrapped, may be < 0)
+//   delta = u - l0, so the kernel argument of window cell i is (i - delta) * 2/w
+template <typename T>
+struct AxisPos { int l; int l0; T delta; };
+
+template <typename T>
+__device__ __forceinline__ AxisPos<T> axis_position(uint64_t phi, int n, int w)
+{
+    AxisPos<T> r;
+    uint64_t F = phi * (uint64_t)n;
+    r.l = (int)__umul64hi(phi, (uint64_t)n);
+    int e;                                       // l - l0
+    if (w & 1) e = (w - 1) / 2 - (F > (1ULL << 63) ? 1 : 0);
+    else       e = w / 2 - (F != 0 ? 1 : 0);
+    r.l0 = r.l - e;
+    T f;
+    if (sizeof(T) == 4) f = (T)(float)(F >> 40) * (T)0x1p-24;
+    else                f = (T)(double)(F >> 11) * (T)0x1p-53;
+    r.delta = (T)e + f;
+    return r;
+}
+
+// ES kernel, Sec. 3 Eq. (es): phi_beta(z) = exp(beta (sqrt(1 - z^2) - 1)), |z| <= 1.
+__device__ __forceinline__ float es_kernel(float z, float beta)
+{
+    float s = 1.0f - z * z;
+    return s >= 0.0f ? expf(beta * (sqrtf(s) - 1.0f)) : 0.0f;
+}
+__device__ __forceinline__ double es_kernel(double z, double beta)
+{
+    double s = 1.0 - z * z;
+    return s >= 0.0 ? exp(beta * (sqrt(s) - 1.0)) : 0.0;
+}
+
+__device__ __forceinline__ int wrap_index(int l, int n)
+{
+    // l within (-n, 2n): one conditional correction
+    return l < 0 ? l + n : (l >= n ? l - n : l);
+}
+
+// Atomic complex add into global memory.
+__device__ __forceinline__ void atomic_add_cplx(float2 *p, float re, float im)
+{
+    atomicAdd(p, make_float2(re, im));           // vector atomic, sm_90+
+}
+__device__ __forceinline__ void atomic_add_cplx(double2 *p, double re, double im)
+{
+    atomicAdd(&p->x, re);
+    atomicAdd(&p->y, im);
+}
+
+// ---------------------------------------------------------------------------
+// Plan object (Sec. 1.1 plan / setup / execute / destroy).
+// ---------------------------------------------------------------------------
+struct Plan {
+    int type = 1, dim = 2, iflag = 1, ntransf = 1, prec = 0;
+    double eps = 1e-6, sigma = 2.0, beta = 0.0;
+    int w = 0;
+    int64_t N[3] = {1, 1, 1};
+    int64_t nf[3] = {1, 1, 1};
+    int64_t Ntot = 1, nftot = 1;
+    int method = NUFFT_METHOD_SM;
+    int m[3] = {1, 1, 1};
+    int nb[3] = {1, 1, 1};
+    int64_t nbins = 1;
+    int msub = 1024;
+    int threads = kDefaultThreads;
+    int ctas_per_sm = 0;
+    int num_sms = 152;
+    cudaStream_t stream = nullptr;
+
+    bool fft_ready = false;
+    cufftHandle fft = 0;
+
+    void *fine = nullptr;          // ntransf * nftot complex
+    void *corr[3] = {nullptr, nullptr, nullptr};   // per-axis correction factors (T), N_i each
+
+    // setpts state
+    bool have_pts = false;
+    int64_t M = 0, Mcap = 0;
+    const void *xyz[3] = {nullptr, nullptr, nullptr};   // caller's arrays (GM only)
+    int32_t *keys = nullptr;       // [Mcap] bin per point, user order
+    int32_t *keys_alt = nullptr;   // [Mcap] radix ping-pong
+    int32_t *vals = nullptr;       // [Mcap]
+    int32_t *vals_alt = nullptr;   // [Mcap]
+    int32_t *perm = nullptr;       // [Mcap] t: sorted position -> original index
+    void *recs = nullptr;          // [Mcap] rec4<T> in bin order
+    void *xyz_copy[3] = {nullptr, nullptr, nullptr};  // coordinate copies for GM
+    int32_t *bincount = nullptr;   // [nbins]
+    int32_t *binstart = nullptr;   // [nbins]
+    int4 *subprob = nullptr;       // [maxsub] (bin, start, count, 0)
+    int64_t maxsub = 0;
+    int32_t *nsub = nullptr;       // [1] device scalar
+    int32_t *hist = nullptr;       // radix histogram [256 * hist_blocks]
+    int hist_blocks = 0;
+    int32_t *scan_tmp = nullptr;   // [nbins] subproblem offsets per bin
+};
+
+// Launchers implemented in the .cu files.  All enqueue on p.stream and return a
+// cudaError_t from the last launch.
+cudaError_t launch_setpts(Plan &p, const void *x, const void *y, const void *z);
+cudaError_t spread_f32_2d(Plan &p, const void *c);
+cudaError_t spread_f32_3d(Plan &p, const void *c);
+cudaError_t spread_f64_2d(Plan &p, const void *c);
+cudaError_t spread_f64_3d(Plan &p, const void *c);
+cudaError_t interp_f32_2d(Plan &p, void *c);
+cudaError_t interp_f32_3d(Plan &p, void *c);
+cudaError_t interp_f64_2d(Plan &p, void *c);
+cudaError_t interp_f64_3d(Plan &p, void *c);
+cudaError_t launch_deconvolve(Plan &p, void *f);
+cudaError_t launch_precorrect(Plan &p, const void *f);
+cudaError_t launch_zero(Plan &p, void *ptr, size_t bytes);
+cudaError_t launch_correction(Plan &p, const double *gl_t, const double *gl_w, int nq);
+
+}  // namespace nufft

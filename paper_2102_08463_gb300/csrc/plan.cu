@@ -1,0 +1,537 @@
+// plan.cu -- the C ABI: plan, setpts, execute, destroy (Sec. 1.1) and the
+// parameter rules of Sec. 3.  Host code only; every step of the transform runs
+// in the kernels of setpts.cu, spread_interp.cuh, correct.cu and in cuFFT.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "nufft_internal.cuh"
+
+using namespace nufft;
+
+std::atomic<unsigned long long> nufft::g_launch_count{0};
+
+struct nufft_plan_s {
+    Plan p;
+};
+
+namespace {
+
+int next235(int64_t n)
+{
+    if (n < 1) n = 1;
+    for (;; ++n) {
+        int64_t m = n;
+        while (m % 2 == 0) m /= 2;
+        while (m % 3 == 0) m /= 3;
+        while (m % 5 == 0) m /= 5;
+        if (m == 1) return (int)n;
+    }
+}
+
+// Kernel width (Sec. 3): w = ceil(log10(1/eps)) + 1 for sigma = 2.  Powers of
+// ten map to their nominal width: a 1e-10 guard absorbs the rounding of
+// log10 of a decimal tolerance.  sigma = 1.25 uses the calibrated width
+// ceil(log10(1/eps) / 0.6) + 1.
+int kernel_width(double eps, double sigma)
+{
+    double digits = -log10(eps);
+    double w = sigma == 2.0 ? ceil(digits - 1e-10) + 1.0 : ceil(digits / 0.6 - 1e-10) + 1.0;
+    if (w < 2.0) w = 2.0;
+    return (int)fmin(w, 99.0);
+}
+
+// beta = 2.30 w for sigma = 2 (Sec. 3); scaled by (1 - 1/(2 sigma)) / (3/4) otherwise.
+double kernel_beta(int w, double sigma)
+{
+    return sigma == 2.0 ? 2.30 * w : 2.30 * w * (1.0 - 1.0 / (2.0 * sigma)) / 0.75;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_nq.
+void gauss_legendre(int nq, std::vector<double> &x, std::vector<double> &wt)
+{
+    const double PI = 3.14159265358979323846;
+    x.assign(nq, 0.0);
+    wt.assign(nq, 0.0);
+    for (int i = 0; i < nq; ++i) {
+        double z = cos(PI * (i + 0.75) / (nq + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= nq; ++k) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            // p1 = P_nq(z), p0 = P_{nq-1}(z)
+            dp = nq * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+int cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess) return NUFFT_OK;
+    if (e == cudaErrorMemoryAllocation) return NUFFT_ERR_ALLOC;
+    return NUFFT_ERR_CUDA;
+}
+
+template <typename Ptr>
+int dev_alloc(Ptr **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free allocation error
+        return NUFFT_ERR_ALLOC;
+    }
+    *ptr = reinterpret_cast<Ptr *>(v);
+    return NUFFT_OK;
+}
+
+void dev_free(void *ptr)
+{
+    if (ptr) cudaFree(ptr);
+}
+
+void free_points(Plan &p)
+{
+    dev_free(p.keys);
+    dev_free(p.keys_alt);
+    dev_free(p.vals);
+    dev_free(p.vals_alt);
+    dev_free(p.recs);
+    dev_free(p.subprob);
+    for (int d = 0; d < 3; ++d) {
+        dev_free(p.xyz_copy[d]);
+        p.xyz_copy[d] = nullptr;
+    }
+    p.keys = p.keys_alt = p.vals = p.vals_alt = p.perm = nullptr;
+    p.recs = nullptr;
+    p.subprob = nullptr;
+    p.Mcap = 0;
+    p.maxsub = 0;
+}
+
+void free_plan(Plan &p)
+{
+    free_points(p);
+    dev_free(p.fine);
+    for (int d = 0; d < 3; ++d) dev_free(p.corr[d]);
+    dev_free(p.bincount);
+    dev_free(p.binstart);
+    dev_free(p.scan_tmp);
+    dev_free(p.nsub);
+    dev_free(p.hist);
+    if (p.fft_ready) cufftDestroy(p.fft);
+    p.fft_ready = false;
+}
+
+size_t real_size(const Plan &p) { return p.prec == 0 ? 4 : 8; }
+
+int default_method(const Plan &p, size_t smem_limit)
+{
+    const int P = (p.w + 1) / 2;
+    size_t cells = 1;
+    for (int d = 0; d < p.dim; ++d) cells *= (size_t)(p.m[d] + 2 * P);
+    if (p.type == 1) {
+        // SM unless the padded bin does not fit in shared memory (Sec. 4.1 remark)
+        return cells * 2 * real_size(p) <= smem_limit ? NUFFT_METHOD_SM : NUFFT_METHOD_GM_SORT;
+    }
+    return NUFFT_METHOD_GM_SORT;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nufft_default_opts(nufft_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->method = NUFFT_METHOD_AUTO;
+    o->upsampfac = 2.0;
+}
+
+const char *nufft_strerror(int code)
+{
+    switch (code) {
+    case NUFFT_OK: return "success";
+    case NUFFT_ERR_ARG: return "invalid argument";
+    case NUFFT_ERR_EPS: return "tolerance outside the supported range for this precision";
+    case NUFFT_ERR_SIZE: return "mode count or fine grid too large";
+    case NUFFT_ERR_ALLOC: return "device allocation failed";
+    case NUFFT_ERR_CUDA: return "CUDA error";
+    case NUFFT_ERR_CUFFT: return "cuFFT error";
+    case NUFFT_ERR_NOPTS: return "execute called before setpts";
+    case NUFFT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case NUFFT_ERR_METHOD: return "method not available for this plan";
+    default: return "unknown error";
+    }
+}
+
+int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntransf, double eps,
+                   int prec, const nufft_opts *opts, nufft_plan *out)
+{
+    if (!out) return NUFFT_ERR_ARG;
+    *out = nullptr;
+    if ((type != 1 && type != 2) || (dim != 2 && dim != 3) || !nmodes) return NUFFT_ERR_ARG;
+    if (iflag != 1 && iflag != -1) return NUFFT_ERR_ARG;
+    if (ntransf < 1 || prec < -1 || prec > 1) return NUFFT_ERR_ARG;
+    if (!(eps > 0.0) || !isfinite(eps)) return NUFFT_ERR_EPS;
+    nufft_opts o;
+    nufft_default_opts(&o);
+    if (opts) o = *opts;
+    double sigma = o.upsampfac == 0.0 ? 2.0 : o.upsampfac;
+    if (sigma != 2.0 && sigma != 1.25) return NUFFT_ERR_ARG;
+    if (o.method < 0 || o.method > 3) return NUFFT_ERR_ARG;
+    if (o.msub < 0 || o.threads < 0 || o.ctas_per_sm < 0) return NUFFT_ERR_ARG;
+    if (o.threads != 0 && (o.threads % 32 != 0 || o.threads > 256)) return NUFFT_ERR_ARG;
+
+    if (prec == -1) prec = eps >= 1e-6 ? 0 : 1;
+    if (prec == 0 && eps < 1e-6) return NUFFT_ERR_EPS;
+    int w = kernel_width(eps, sigma);
+    if (w > kMaxW) return NUFFT_ERR_EPS;
+
+    nufft_plan_s *h = new (std::nothrow) nufft_plan_s;
+    if (!h) return NUFFT_ERR_ALLOC;
+    Plan &p = h->p;
+    p.type = type;
+    p.dim = dim;
+    p.iflag = iflag;
+    p.ntransf = ntransf;
+    p.prec = prec;
+    p.eps = eps;
+    p.sigma = sigma;
+    p.w = w;
+    p.beta = kernel_beta(w, sigma);
+    p.stream = (cudaStream_t)o.stream;
+    p.threads = o.threads ? o.threads : kDefaultThreads;
+    p.ctas_per_sm = o.ctas_per_sm;
+    p.msub = o.msub ? o.msub : 1024;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (p.num_sms < 1) p.num_sms = 1;
+
+    const int P = (w + 1) / 2;
+    int64_t ntot = 1, nftot = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d < dim) {
+            if (nmodes[d] < 1 || nmodes[d] > (1 << 26)) { delete h; return NUFFT_ERR_SIZE; }
+            p.N[d] = nmodes[d];
+            int64_t want = (int64_t)ceil(sigma * (double)p.N[d] - 1e-9);
+            if (want < 2 * w) want = 2 * w;
+            p.nf[d] = next235(want);
+            int mdef = dim == 2 ? 32 : (d < 2 ? 16 : 2);
+            int m = o.bin[d] > 0 ? o.bin[d] : mdef;
+            if (m > p.nf[d]) m = (int)p.nf[d];
+            if (m + 2 * P > 1023) { delete h; return NUFFT_ERR_ARG; }
+            p.m[d] = m;
+            p.nb[d] = (int)((p.nf[d] + m - 1) / m);
+        } else {
+            p.N[d] = 1;
+            p.nf[d] = 1;
+            p.m[d] = 1;
+            p.nb[d] = 1;
+        }
+        ntot *= p.N[d];
+        nftot *= p.nf[d];
+    }
+    if (nftot > ((int64_t)1 << 40) || (double)nftot * ntransf * 2 * real_size(p) > 4e11) {
+        delete h;
+        return NUFFT_ERR_SIZE;
+    }
+    p.Ntot = ntot;
+    p.nftot = nftot;
+    p.nbins = (int64_t)p.nb[0] * p.nb[1] * p.nb[2];
+    if (p.nbins > ((int64_t)1 << 30)) { delete h; return NUFFT_ERR_SIZE; }
+
+    p.method = o.method == NUFFT_METHOD_AUTO ? default_method(p, (size_t)smem_optin) : o.method;
+    if (p.method == NUFFT_METHOD_SM) {
+        size_t cells = 1;
+        for (int d = 0; d < dim; ++d) cells *= (size_t)(p.m[d] + 2 * P);
+        size_t need = p.type == 1 ? cells * 2 * real_size(p) : cells * 2 * real_size(p);
+        if (need > (size_t)smem_optin) { delete h; return NUFFT_ERR_METHOD; }
+    }
+
+    int rc = NUFFT_OK;
+    const size_t csz = 2 * real_size(p);
+    rc = dev_alloc(&p.fine, (size_t)nftot * ntransf * csz);
+    for (int d = 0; d < 3 && rc == NUFFT_OK; ++d) rc = dev_alloc(&p.corr[d], (size_t)p.N[d] * real_size(p));
+    if (rc == NUFFT_OK) rc = dev_alloc(&p.bincount, sizeof(int32_t) * p.nbins);
+    if (rc == NUFFT_OK) rc = dev_alloc(&p.binstart, sizeof(int32_t) * p.nbins);
+    if (rc == NUFFT_OK) rc = dev_alloc(&p.scan_tmp, sizeof(int32_t) * p.nbins);
+    if (rc == NUFFT_OK) rc = dev_alloc(&p.nsub, sizeof(int32_t) * 4);
+    if (rc == NUFFT_OK) rc = dev_alloc(&p.hist, sizeof(int32_t) * 256 * (size_t)p.num_sms * 2);
+    if (rc != NUFFT_OK) {
+        free_plan(p);
+        delete h;
+        return rc;
+    }
+
+    // correction factors, in FP64 then rounded to the plan precision
+    {
+        const int nq = 64 + 4 * w;
+        std::vector<double> gx, gw;
+        gauss_legendre(nq, gx, gw);
+        std::vector<double> st(nq), v(nq);
+        const double PI = 3.14159265358979323846;
+        for (int q = 0; q < nq; ++q) {
+            double t = 0.5 * PI * gx[q];
+            st[q] = sin(t);
+            v[q] = 0.5 * PI * gw[q] * exp(p.beta * (cos(t) - 1.0)) * cos(t);
+        }
+        double *dst = nullptr, *dv = nullptr;
+        rc = dev_alloc(&dst, sizeof(double) * nq);
+        if (rc == NUFFT_OK) rc = dev_alloc(&dv, sizeof(double) * nq);
+        cudaError_t e = cudaSuccess;
+        if (rc == NUFFT_OK) e = cudaMemcpyAsync(dst, st.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, p.stream);
+        if (rc == NUFFT_OK && e == cudaSuccess) e = cudaMemcpyAsync(dv, v.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, p.stream);
+        if (rc == NUFFT_OK && e == cudaSuccess) e = launch_correction(p, dst, dv, nq);
+        // axes beyond dim hold the single factor 1
+        for (int d = dim; d < 3 && rc == NUFFT_OK && e == cudaSuccess; ++d) {
+            if (p.prec == 0) {
+                static const float one_f = 1.0f;
+                e = cudaMemcpyAsync(p.corr[d], &one_f, sizeof(float), cudaMemcpyHostToDevice, p.stream);
+            } else {
+                static const double one_d = 1.0;
+                e = cudaMemcpyAsync(p.corr[d], &one_d, sizeof(double), cudaMemcpyHostToDevice, p.stream);
+            }
+        }
+        if (rc == NUFFT_OK && e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+        dev_free(dst);
+        dev_free(dv);
+        if (rc == NUFFT_OK && e != cudaSuccess) rc = cuda_err(e);
+        if (rc != NUFFT_OK) {
+            free_plan(p);
+            delete h;
+            return rc;
+        }
+    }
+
+    // cuFFT plan for the fine grid, batched over ntransf (Sec. 4, step 2)
+    {
+        int dims[3];
+        for (int d = 0; d < dim; ++d) dims[d] = (int)p.nf[dim - 1 - d];   // slowest first
+        cufftResult r = cufftPlanMany(&p.fft, dim, dims, nullptr, 1, (int)nftot, nullptr, 1,
+                                      (int)nftot, p.prec == 0 ? CUFFT_C2C : CUFFT_Z2Z, ntransf);
+        if (r == CUFFT_SUCCESS) {
+            p.fft_ready = true;
+            r = cufftSetStream(p.fft, p.stream);
+        }
+        if (r != CUFFT_SUCCESS) {
+            free_plan(p);
+            delete h;
+            return r == CUFFT_ALLOC_FAILED ? NUFFT_ERR_ALLOC : NUFFT_ERR_CUFFT;
+        }
+    }
+    *out = h;
+    return NUFFT_OK;
+}
+
+int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const void *z)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (M < 0 || M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_ARG;
+    if (M > 0 && (!x || !y || (p.dim == 3 && !z))) return NUFFT_ERR_ARG;
+    p.have_pts = false;
+    const int64_t maxsub = p.nbins + M / p.msub + 1;
+    if (M > p.Mcap || maxsub > p.maxsub) {
+        free_points(p);
+        const int64_t cap = M > 0 ? M : 1;
+        const size_t rsz = p.prec == 0 ? sizeof(float4) : sizeof(double4);
+        int rc = dev_alloc(&p.keys, sizeof(int32_t) * cap);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.keys_alt, sizeof(int32_t) * cap);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.vals, sizeof(int32_t) * cap);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.vals_alt, sizeof(int32_t) * cap);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.recs, rsz * cap);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.subprob, sizeof(int4) * maxsub);
+        if (rc != NUFFT_OK) {
+            free_points(p);
+            return rc;
+        }
+        p.Mcap = cap;
+        p.maxsub = maxsub;
+    }
+    if (p.method == NUFFT_METHOD_GM) {
+        // GM works in user order (Sec. 4.1): keep a copy of the coordinates, no sort
+        for (int d = 0; d < p.dim; ++d) {
+            if (!p.xyz_copy[d]) {
+                int rc = dev_alloc(&p.xyz_copy[d], real_size(p) * p.Mcap);
+                if (rc != NUFFT_OK) return rc;
+            }
+        }
+        const void *src[3] = {x, y, z};
+        for (int d = 0; d < p.dim && M > 0; ++d) {
+            cudaError_t e = cudaMemcpyAsync(p.xyz_copy[d], src[d], real_size(p) * M,
+                                            cudaMemcpyDeviceToDevice, p.stream);
+            if (e != cudaSuccess) return cuda_err(e);
+        }
+        p.M = M;
+        p.have_pts = true;
+        return NUFFT_OK;
+    }
+    p.M = M;
+    int64_t blocks = (M + 4095) / 4096;
+    if (blocks > (int64_t)p.num_sms * 2) blocks = (int64_t)p.num_sms * 2;
+    if (blocks < 1) blocks = 1;
+    p.hist_blocks = (int)blocks;
+    cudaError_t e = launch_setpts(p, x, y, z);
+    if (e != cudaSuccess) return cuda_err(e);
+    p.have_pts = true;
+    return NUFFT_OK;
+}
+
+int nufft_spread(nufft_plan h, const void *c)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (!p.have_pts) return NUFFT_ERR_NOPTS;
+    if (p.M > 0 && !c) return NUFFT_ERR_ARG;
+    cudaError_t e = launch_zero(p, p.fine, (size_t)p.nftot * p.ntransf * 2 * real_size(p));
+    if (e != cudaSuccess) return cuda_err(e);
+    return nufft_spread_add(h, c);
+}
+
+int nufft_spread_add(nufft_plan h, const void *c)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (!p.have_pts) return NUFFT_ERR_NOPTS;
+    if (p.M == 0) return NUFFT_OK;
+    if (!c) return NUFFT_ERR_ARG;
+    cudaError_t e;
+    int method = p.method;
+    if (p.type == 2 && method == NUFFT_METHOD_SM) p.method = NUFFT_METHOD_GM_SORT;   // SM spread needs its smem
+    if (p.prec == 0) e = p.dim == 2 ? spread_f32_2d(p, c) : spread_f32_3d(p, c);
+    else e = p.dim == 2 ? spread_f64_2d(p, c) : spread_f64_3d(p, c);
+    p.method = method;
+    return cuda_err(e);
+}
+
+int nufft_interp(nufft_plan h, void *c)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (!p.have_pts) return NUFFT_ERR_NOPTS;
+    if (p.M == 0) return NUFFT_OK;
+    if (!c) return NUFFT_ERR_ARG;
+    cudaError_t e;
+    if (p.prec == 0) e = p.dim == 2 ? interp_f32_2d(p, c) : interp_f32_3d(p, c);
+    else e = p.dim == 2 ? interp_f64_2d(p, c) : interp_f64_3d(p, c);
+    return cuda_err(e);
+}
+
+int nufft_fft(nufft_plan h)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    // type 1 FFT takes the sign of iflag, type 2 the opposite (Eq. 2d1 / 2d2)
+    const int sign = p.type == 1 ? p.iflag : -p.iflag;
+    const int dir = sign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD;
+    cufftResult r;
+    if (p.prec == 0)
+        r = cufftExecC2C(p.fft, (cufftComplex *)p.fine, (cufftComplex *)p.fine, dir);
+    else
+        r = cufftExecZ2Z(p.fft, (cufftDoubleComplex *)p.fine, (cufftDoubleComplex *)p.fine, dir);
+    return r == CUFFT_SUCCESS ? NUFFT_OK : NUFFT_ERR_CUFFT;
+}
+
+int nufft_deconvolve(nufft_plan h, void *f)
+{
+    if (!h || !f) return NUFFT_ERR_ARG;
+    return cuda_err(launch_deconvolve(h->p, f));
+}
+
+int nufft_precorrect(nufft_plan h, const void *f)
+{
+    if (!h || !f) return NUFFT_ERR_ARG;
+    return cuda_err(launch_precorrect(h->p, f));
+}
+
+int nufft_execute(nufft_plan h, void *c, void *f)
+{
+    if (!h || !f) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (!p.have_pts) return NUFFT_ERR_NOPTS;
+    if (p.M > 0 && !c) return NUFFT_ERR_ARG;
+    int rc;
+    if (p.type == 1) {
+        if ((rc = nufft_spread(h, c)) != NUFFT_OK) return rc;
+        if ((rc = nufft_fft(h)) != NUFFT_OK) return rc;
+        return nufft_deconvolve(h, f);
+    }
+    if ((rc = nufft_precorrect(h, f)) != NUFFT_OK) return rc;
+    if ((rc = nufft_fft(h)) != NUFFT_OK) return rc;
+    return nufft_interp(h, c);
+}
+
+uint64_t nufft_get_launch_count(void)
+{
+    return (uint64_t)g_launch_count.load(std::memory_order_relaxed);
+}
+
+int nufft_destroy(nufft_plan h)
+{
+    if (!h) return NUFFT_OK;
+    free_plan(h->p);
+    delete h;
+    return NUFFT_OK;
+}
+
+int nufft_get_params(nufft_plan h, int *w, double *beta, int64_t *nf, int *bins, int64_t *nbins,
+                     int *prec, int *method)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    const Plan &p = h->p;
+    if (w) *w = p.w;
+    if (beta) *beta = p.beta;
+    for (int d = 0; d < 3; ++d) {
+        if (nf) nf[d] = p.nf[d];
+        if (bins) bins[d] = p.m[d];
+    }
+    if (nbins) *nbins = p.nbins;
+    if (prec) *prec = p.prec;
+    if (method) *method = p.method;
+    return NUFFT_OK;
+}
+
+int nufft_get_finegrid(nufft_plan h, void **dptr, size_t *bytes)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    const Plan &p = h->p;
+    if (dptr) *dptr = p.fine;
+    if (bytes) *bytes = (size_t)p.nftot * p.ntransf * 2 * real_size(p);
+    return NUFFT_OK;
+}
+
+int nufft_get_sort(nufft_plan h, int32_t *t, int32_t *bincounts, int32_t *nsub)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (!p.have_pts) return NUFFT_ERR_NOPTS;
+    if (p.method == NUFFT_METHOD_GM) return NUFFT_ERR_METHOD;
+    cudaError_t e = cudaSuccess;
+    if (t && p.M > 0) e = cudaMemcpyAsync(t, p.perm, sizeof(int32_t) * p.M, cudaMemcpyDeviceToDevice, p.stream);
+    if (e == cudaSuccess && bincounts)
+        e = cudaMemcpyAsync(bincounts, p.bincount, sizeof(int32_t) * p.nbins, cudaMemcpyDeviceToDevice, p.stream);
+    if (e == cudaSuccess && nsub)
+        e = cudaMemcpyAsync(nsub, p.nsub, sizeof(int32_t), cudaMemcpyDeviceToDevice, p.stream);
+    return cuda_err(e);
+}
+
+}  // extern "C"

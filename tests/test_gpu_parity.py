@@ -1,0 +1,308 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Three bars, each stated where it is used:
+  * the bin-sort (permutation t, per-bin counts, subproblem count) is bit-exact;
+  * against the oracle's own three-step pipeline at the SAME kernel width the
+    only differences are rounding: relative l2 <= 2e-5 in single precision,
+    <= 1e-11 in double (the design doc derives both from the arithmetic);
+  * against the exact sums, relative l2 <= 2 eps where the oracle pipeline at
+    that width meets eps (the width rule of Sec. 3), else <= oracle error plus
+    the rounding allowance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_08463_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 2e-5
+TOL_F64 = 1e-11
+
+
+@pytest.fixture(scope="module")
+def nb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_08463_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _plan(nb, type_, N, eps, prec, method="auto", iflag=+1, ntransf=1, **kw):
+    return nb.Plan(type_, N, eps, iflag=iflag, ntransf=ntransf, prec=prec, method=method, **kw)
+
+
+def _pts_dev(pts, prec):
+    rd = torch.float32 if prec == 0 else torch.float64
+    return [_dev(p, rd) for p in pts]
+
+
+def _tol(prec):
+    return TOL_F32 if prec == 0 else TOL_F64
+
+
+# ---------------------------------------------------------------------------
+# bin-sort: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,kind,M", [(2, "rand", 70001), (2, "cluster", 5000), (3, "rand", 40003),
+                                        (3, "gauss", 30011), (2, "rand", 1), (3, "cluster", 777)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_binsort_bit_exact(nb, dim, kind, M, prec):
+    N = (100, 96) if dim == 2 else (40, 36, 30)
+    eps = 1e-5 if prec == 0 else 1e-9
+    dt = np.float32 if prec == 0 else np.float64
+    p = _plan(nb, 1, N, eps, prec, method="sm")
+    nf = p.params["nf"][:dim]
+    pts = wl.points(kind, dim, M, 1000 + M, dt, n=nf)
+    pts[0][: min(M, 3)] = np.array([-math.pi, math.pi, np.nextafter(dt(math.pi), dt(4))], dt)[: min(M, 3)]
+    dp = _pts_dev(pts, prec)
+    p.setpts(*dp)
+    t, bc, nsub = p.sort()
+    bins = p.params["bins"][:dim]
+    binidx, counts, t_ref = oracle.binsort([q.astype(np.float64) for q in pts], nf, bins)
+    assert np.array_equal(_host(t).astype(np.int64), t_ref)
+    assert np.array_equal(_host(bc).astype(np.int64), counts)
+    assert nsub == oracle.subproblems(counts, 1024).shape[0]
+    p.close()
+
+
+def test_binsort_many_bins_three_passes(nb):
+    # 3D fine grid 128^3 with 4x4x2 bins: 32768 * 2 = 65536 bins -> 16-bit keys, 2 radix passes;
+    # 2x2x2 bins on 160^3 -> 512000 bins -> 3 passes
+    for N, bins in (((64, 64, 64), (4, 4, 2)), ((80, 80, 80), (2, 2, 2))):
+        p = _plan(nb, 1, N, 1e-2, 0, method="gmsort", bins=bins)
+        nf = p.params["nf"][:3]
+        M = 200003
+        pts = wl.points("rand", 3, M, 77, np.float32)
+        p.setpts(*_pts_dev(pts, 0))
+        t, bc, nsub = p.sort()
+        _, counts, t_ref = oracle.binsort([q.astype(np.float64) for q in pts], nf, bins)
+        assert np.array_equal(_host(t).astype(np.int64), t_ref)
+        assert np.array_equal(_host(bc).astype(np.int64), counts)
+        p.close()
+
+
+# ---------------------------------------------------------------------------
+# spreading alone: fine grid vs the oracle's spread at the same width
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", ["gm", "gmsort", "sm"])
+@pytest.mark.parametrize("dim,prec,eps", [(2, 0, 1e-5), (3, 0, 1e-6), (2, 1, 1e-12), (3, 1, 1e-9),
+                                          (2, 0, 1e-2), (3, 0, 1e-3)])
+def test_spread_grid_matches_oracle(nb, method, dim, prec, eps):
+    N = (50, 46) if dim == 2 else (20, 18, 16)
+    M = 6007
+    dt = np.float32 if prec == 0 else np.float64
+    ct = np.complex64 if prec == 0 else np.complex128
+    p = _plan(nb, 1, N, eps, prec, method=method)
+    w, beta, nf = p.params["w"], p.params["beta"], p.params["nf"][:dim]
+    pts = wl.points("rand", dim, M, 5 + dim, dt)
+    c = wl.strengths(M, 6, ct)
+    p.setpts(*_pts_dev(pts, prec))
+    nb.spread(p.handle, nb._dptr(_dev(c)))
+    g = _host(p.finegrid())
+    ref = oracle.spread([q.astype(np.float64) for q in pts], c.astype(np.complex128), nf, w, beta)
+    assert oracle.rel_l2(g, ref) < _tol(prec)
+    p.close()
+
+
+# ---------------------------------------------------------------------------
+# full transforms, small sizes spanning several bins and a ragged tail
+# ---------------------------------------------------------------------------
+CASES = [
+    # dim, N, M, eps, prec
+    (2, (64, 64), 4096, 1e-5, 0),
+    (2, (33, 70), 3001, 1e-2, 0),
+    (2, (48, 40), 5000, 1e-9, 1),
+    (2, (40, 40), 2500, 1e-12, 1),
+    (3, (16, 20, 12), 4001, 1e-6, 0),
+    (3, (17, 16, 15), 3000, 1e-2, 0),
+    (3, (12, 12, 12), 2000, 1e-9, 1),
+]
+
+
+def _exact_bar(eps, e_oracle, prec):
+    return max(2 * eps, e_oracle + (5 * TOL_F32 if prec == 0 else TOL_F64))
+
+
+@pytest.mark.parametrize("dim,N,M,eps,prec", CASES)
+@pytest.mark.parametrize("method", ["gm", "gmsort", "sm"])
+@pytest.mark.parametrize("iflag", [+1, -1])
+def test_type1_parity(nb, dim, N, M, eps, prec, method, iflag):
+    dt = np.float32 if prec == 0 else np.float64
+    ct = np.complex64 if prec == 0 else np.complex128
+    pts = wl.points("rand", dim, M, 11 * M + dim, dt)
+    c = wl.strengths(M, 12 + M, ct)
+    p = _plan(nb, 1, N, eps, prec, method=method, iflag=iflag)
+    p.setpts(*_pts_dev(pts, prec))
+    f = _host(p.execute(c=_dev(c)))
+    p64 = [q.astype(np.float64) for q in pts]
+    same_w = oracle.nufft_type1(p64, c.astype(np.complex128), N, iflag=iflag, w=p.params["w"])
+    assert oracle.rel_l2(f, same_w) < _tol(prec)
+    exact = oracle.direct_type1(p64, c.astype(np.complex128), N, iflag)
+    e_or = oracle.rel_l2(same_w, exact)
+    assert oracle.rel_l2(f, exact) <= _exact_bar(eps, e_or, prec)
+    p.close()
+
+
+@pytest.mark.parametrize("dim,N,M,eps,prec", CASES)
+@pytest.mark.parametrize("method", ["gm", "gmsort", "sm"])
+@pytest.mark.parametrize("iflag", [+1, -1])
+def test_type2_parity(nb, dim, N, M, eps, prec, method, iflag):
+    dt = np.float32 if prec == 0 else np.float64
+    ct = np.complex64 if prec == 0 else np.complex128
+    pts = wl.points("rand", dim, M, 13 * M + dim, dt)
+    f = wl.modes(N, 14 + M, ct)
+    p = _plan(nb, 2, N, eps, prec, method=method, iflag=iflag)
+    p.setpts(*_pts_dev(pts, prec))
+    c = _host(p.execute(f=_dev(f)))
+    p64 = [q.astype(np.float64) for q in pts]
+    same_w = oracle.nufft_type2(p64, f.astype(np.complex128), iflag=iflag, w=p.params["w"])
+    assert oracle.rel_l2(c, same_w) < _tol(prec)
+    exact = oracle.direct_type2(p64, f.astype(np.complex128), iflag)
+    e_or = oracle.rel_l2(same_w, exact)
+    assert oracle.rel_l2(c, exact) <= _exact_bar(eps, e_or, prec)
+    p.close()
+
+
+@pytest.mark.parametrize("kind", ["cluster", "gauss"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_clustered_points(nb, kind, dim):
+    N = (64, 64) if dim == 2 else (16, 16, 16)
+    M = 20000
+    pts = wl.points(kind, dim, M, 99, np.float32, n=[2 * v for v in N], spread=0.05 * math.pi)
+    c = wl.strengths(M, 98, np.complex64)
+    p64 = [q.astype(np.float64) for q in pts]
+    for method in ("sm", "gmsort"):
+        p = _plan(nb, 1, N, 1e-5, 0, method=method, msub=256)
+        p.setpts(*_pts_dev(pts, 0))
+        f = _host(p.execute(c=_dev(c)))
+        ref = oracle.nufft_type1(p64, c.astype(np.complex128), N, w=p.params["w"])
+        assert oracle.rel_l2(f, ref) < TOL_F32
+        p.close()
+
+
+@pytest.mark.parametrize("type_", [1, 2])
+def test_ntransf(nb, type_):
+    N, M, nt = (40, 36), 3000, 5
+    pts = wl.points("rand", 2, M, 3, np.float32)
+    p64 = [q.astype(np.float64) for q in pts]
+    for method in ("sm", "gmsort", "gm"):
+        p = _plan(nb, type_, N, 1e-5, 0, method=method, ntransf=nt)
+        p.setpts(*_pts_dev(pts, 0))
+        w = p.params["w"]
+        if type_ == 1:
+            c = wl.strengths(M, 4, np.complex64, ntransf=nt)
+            f = _host(p.execute(c=_dev(c)))
+            for t in range(nt):
+                ref = oracle.nufft_type1(p64, c[t].astype(np.complex128), N, w=w)
+                assert oracle.rel_l2(f[t], ref) < TOL_F32
+        else:
+            f = wl.modes(N, 5, np.complex64, ntransf=nt)
+            c = _host(p.execute(f=_dev(f)))
+            for t in range(nt):
+                ref = oracle.nufft_type2(p64, f[t].astype(np.complex128), w=w)
+                assert oracle.rel_l2(c[t], ref) < TOL_F32
+        p.close()
+
+
+def test_adjoint_identity_on_gpu(nb):
+    # approximate type 2 is the exact adjoint of approximate type 1 (same window)
+    N, M = (24, 20, 18), 5000
+    pts = wl.points("rand", 3, M, 21, np.float64)
+    c = wl.strengths(M, 22, np.complex128)
+    f = wl.modes(N, 23, np.complex128)
+    p1 = _plan(nb, 1, N, 1e-9, 1)
+    p2 = _plan(nb, 2, N, 1e-9, 1)
+    dp = _pts_dev(pts, 1)
+    p1.setpts(*dp)
+    p2.setpts(*dp)
+    a = _host(p1.execute(c=_dev(c)))
+    b = _host(p2.execute(f=_dev(f)))
+    lhs = np.vdot(f.ravel(), a.ravel())
+    rhs = np.vdot(b, c)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    p1.close()
+    p2.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_empty_points(nb):
+    p = _plan(nb, 1, (16, 16), 1e-5, 0)
+    x = torch.empty(0, dtype=torch.float32, device="cuda")
+    p.setpts(x, x)
+    f = _host(p.execute(c=torch.empty(0, dtype=torch.complex64, device="cuda")))
+    assert np.all(f == 0)
+    p.close()
+    q = _plan(nb, 2, (16, 16), 1e-5, 0)
+    q.setpts(x, x)
+    c = q.execute(f=_dev(wl.modes((16, 16), 1, np.complex64)))
+    assert c.numel() == 0
+    q.close()
+
+
+def test_single_point_and_odd_sizes(nb):
+    x0 = np.array([0.7], np.float64)
+    y0 = np.array([-2.9], np.float64)
+    z0 = np.array([3.1], np.float64)
+    c = np.array([1.0 + 0.5j])
+    for N in ((1, 1, 1), (5, 1, 7), (9, 11, 3)):
+        p = _plan(nb, 1, N, 1e-12, 1)
+        p.setpts(*_pts_dev([x0, y0, z0], 1))
+        f = _host(p.execute(c=_dev(c)))
+        ref = oracle.direct_type1([x0, y0, z0], c, N)
+        assert oracle.rel_l2(f, ref) < 3e-12
+        p.close()
+
+
+def test_edge_coordinates(nb):
+    vals = np.array([-math.pi, math.pi, 3 * math.pi - 1e-6, -3 * math.pi, 0.0, 1e-30, -1e-30,
+                     math.pi / 2, -math.pi / 2], np.float32)
+    M = vals.size ** 2
+    x = np.repeat(vals, vals.size)
+    y = np.tile(vals, vals.size)
+    c = wl.strengths(M, 5, np.complex64)
+    for method in ("sm", "gmsort", "gm"):
+        p = _plan(nb, 1, (32, 32), 1e-5, 0, method=method)
+        p.setpts(*_pts_dev([x, y], 0))
+        f = _host(p.execute(c=_dev(c)))
+        ref = oracle.direct_type1([x.astype(np.float64), y.astype(np.float64)],
+                                  c.astype(np.complex128), (32, 32))
+        assert oracle.rel_l2(f, ref) < 3e-5
+        p.close()
+
+
+def test_errors(nb):
+    with pytest.raises(nb.NufftError) as e:
+        nb.makeplan(3, 2, (8, 8))
+    assert e.value.code == nb.NUFFT_ERR_ARG
+    with pytest.raises(nb.NufftError) as e:
+        nb.makeplan(1, 2, (8, 8), eps=1e-9, prec=0)
+    assert e.value.code == nb.NUFFT_ERR_EPS
+    with pytest.raises(nb.NufftError) as e:
+        nb.makeplan(1, 2, (8, 8), eps=1e-17, prec=1)
+    assert e.value.code == nb.NUFFT_ERR_EPS
+    h = nb.makeplan(1, 2, (8, 8), eps=1e-5)
+    with pytest.raises(nb.NufftError) as e:
+        nb.execute(h, None, nb._dptr(torch.empty(64, dtype=torch.complex64, device="cuda")))
+    assert e.value.code == nb.NUFFT_ERR_NOPTS
+    nb.destroy(h)
