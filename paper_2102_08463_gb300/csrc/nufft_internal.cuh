@@ -24,7 +24,7 @@ template <typename T> struct cplx;
 template <> struct cplx<float> { using type = float2; };
 template <> struct cplx<double> { using type = double2; };
 
-// Packed per-point record in bin order: kernel offsets delta_i = u_i - l0_i
+// Packed per-point record: kernel offsets delta_i = u_i - l0_i
 // (u_i the fine-grid coordinate, l0_i the first window cell) and the window
 // start relative to the padded bin, three 10-bit fields in one 32-bit word
 // stored in the last slot.
@@ -101,6 +101,13 @@ __device__ __forceinline__ AxisPos<T> axis_position(uint64_t phi, int n, int w)
     return r;
 }
 
+// Padded bin of Sec. 4.1 SM step 2: a point whose cell lies in a bin of m
+// cells has its w-cell window inside the m + w cells starting floor(w/2) before
+// the bin origin (the paper's p_i = m_i + 2 ceil(w/2) is one cell larger for
+// odd w; the window never reaches that cell).
+__host__ __device__ __forceinline__ int pad_lo(int w) { return w / 2; }
+__host__ __device__ __forceinline__ int padded(int m, int w) { return m + w; }
+
 // ES kernel, Sec. 3 Eq. (es): phi_beta(z) = exp(beta (sqrt(1 - z^2) - 1)), |z| <= 1.
 __device__ __forceinline__ float es_kernel(float z, float beta)
 {
@@ -165,21 +172,29 @@ struct Plan {
     int32_t *vals = nullptr;       // [Mcap]
     int32_t *vals_alt = nullptr;   // [Mcap]
     int32_t *perm = nullptr;       // [Mcap] t: sorted position -> original index
-    void *recs = nullptr;          // [Mcap] rec4<T> in bin order
+    void *recs = nullptr;          // [Mcap] rec4<T> per point, original order
     void *xyz_copy[3] = {nullptr, nullptr, nullptr};  // coordinate copies for GM
     int32_t *bincount = nullptr;   // [nbins]
     int32_t *binstart = nullptr;   // [nbins]
     int4 *subprob = nullptr;       // [maxsub] (bin, start, count, 0)
     int64_t maxsub = 0;
     int32_t *nsub = nullptr;       // [1] device scalar
-    int32_t *hist = nullptr;       // radix histogram [256 * hist_blocks]
-    int hist_blocks = 0;
+    int32_t *mat = nullptr;        // sort histogram matrix (bins or digits) x CTAs
+    int64_t mat_cap = 0;
+    int32_t *scan_part = nullptr;  // block sums of the multi-block scan
+    int64_t scan_part_cap = 0;
     int32_t *scan_tmp = nullptr;   // [nbins] subproblem offsets per bin
+    int smem_optin = 0;            // max dynamic shared memory per CTA (bytes)
+    int smem_per_sm = 0;           // shared memory per SM (bytes)
 };
 
 // Launchers implemented in the .cu files.  All enqueue on p.stream and return a
 // cudaError_t from the last launch.
 cudaError_t launch_setpts(Plan &p, const void *x, const void *y, const void *z);
+cudaError_t launch_scan(Plan &p, const int32_t *in, int32_t *out, int64_t L, int32_t *total);
+int64_t scan_parts_needed(int64_t L);
+int counting_sort_blocks(const Plan &p, int64_t M);
+int radix_sort_blocks(const Plan &p, int64_t M);
 cudaError_t spread_f32_2d(Plan &p, const void *c);
 cudaError_t spread_f32_3d(Plan &p, const void *c);
 cudaError_t spread_f64_2d(Plan &p, const void *c);

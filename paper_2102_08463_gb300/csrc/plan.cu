@@ -132,7 +132,10 @@ void free_plan(Plan &p)
     dev_free(p.binstart);
     dev_free(p.scan_tmp);
     dev_free(p.nsub);
-    dev_free(p.hist);
+    dev_free(p.mat);
+    dev_free(p.scan_part);
+    p.mat = p.scan_part = nullptr;
+    p.mat_cap = p.scan_part_cap = 0;
     if (p.fft_ready) cufftDestroy(p.fft);
     p.fft_ready = false;
 }
@@ -141,14 +144,11 @@ size_t real_size(const Plan &p) { return p.prec == 0 ? 4 : 8; }
 
 int default_method(const Plan &p, size_t smem_limit)
 {
-    const int P = (p.w + 1) / 2;
     size_t cells = 1;
-    for (int d = 0; d < p.dim; ++d) cells *= (size_t)(p.m[d] + 2 * P);
-    if (p.type == 1) {
-        // SM unless the padded bin does not fit in shared memory (Sec. 4.1 remark)
-        return cells * 2 * real_size(p) <= smem_limit ? NUFFT_METHOD_SM : NUFFT_METHOD_GM_SORT;
-    }
-    return NUFFT_METHOD_GM_SORT;
+    for (int d = 0; d < p.dim; ++d) cells *= (size_t)padded(p.m[d], p.w);
+    // SM (type 1: shared-memory subproblems; type 2: padded bin staged in shared
+    // memory) unless the padded bin does not fit (Sec. 4.1 remark on 3D fp64)
+    return cells * 2 * real_size(p) <= smem_limit ? NUFFT_METHOD_SM : NUFFT_METHOD_GM_SORT;
 }
 
 }  // namespace
@@ -224,9 +224,10 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&p.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (p.num_sms < 1) p.num_sms = 1;
+    p.smem_optin = smem_optin;
 
-    const int P = (w + 1) / 2;
     int64_t ntot = 1, nftot = 1;
     for (int d = 0; d < 3; ++d) {
         if (d < dim) {
@@ -235,10 +236,10 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
             int64_t want = (int64_t)ceil(sigma * (double)p.N[d] - 1e-9);
             if (want < 2 * w) want = 2 * w;
             p.nf[d] = next235(want);
-            int mdef = dim == 2 ? 32 : (d < 2 ? 16 : 2);
+            int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
             int m = o.bin[d] > 0 ? o.bin[d] : mdef;
             if (m > p.nf[d]) m = (int)p.nf[d];
-            if (m + 2 * P > 1023) { delete h; return NUFFT_ERR_ARG; }
+            if (padded(m, w) > 1023) { delete h; return NUFFT_ERR_ARG; }
             p.m[d] = m;
             p.nb[d] = (int)((p.nf[d] + m - 1) / m);
         } else {
@@ -262,8 +263,8 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     p.method = o.method == NUFFT_METHOD_AUTO ? default_method(p, (size_t)smem_optin) : o.method;
     if (p.method == NUFFT_METHOD_SM) {
         size_t cells = 1;
-        for (int d = 0; d < dim; ++d) cells *= (size_t)(p.m[d] + 2 * P);
-        size_t need = p.type == 1 ? cells * 2 * real_size(p) : cells * 2 * real_size(p);
+        for (int d = 0; d < dim; ++d) cells *= (size_t)padded(p.m[d], w);
+        size_t need = cells * 2 * real_size(p);
         if (need > (size_t)smem_optin) { delete h; return NUFFT_ERR_METHOD; }
     }
 
@@ -275,7 +276,6 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     if (rc == NUFFT_OK) rc = dev_alloc(&p.binstart, sizeof(int32_t) * p.nbins);
     if (rc == NUFFT_OK) rc = dev_alloc(&p.scan_tmp, sizeof(int32_t) * p.nbins);
     if (rc == NUFFT_OK) rc = dev_alloc(&p.nsub, sizeof(int32_t) * 4);
-    if (rc == NUFFT_OK) rc = dev_alloc(&p.hist, sizeof(int32_t) * 256 * (size_t)p.num_sms * 2);
     if (rc != NUFFT_OK) {
         free_plan(p);
         delete h;
@@ -386,10 +386,30 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
         return NUFFT_OK;
     }
     p.M = M;
-    int64_t blocks = (M + 4095) / 4096;
-    if (blocks > (int64_t)p.num_sms * 2) blocks = (int64_t)p.num_sms * 2;
-    if (blocks < 1) blocks = 1;
-    p.hist_blocks = (int)blocks;
+    // sort matrix and scan scratch for this M
+    {
+        const int cblk = counting_sort_blocks(p, M > 0 ? M : 1);
+        const int rblk = radix_sort_blocks(p, M > 0 ? M : 1);
+        int64_t mat = cblk > 0 ? p.nbins * cblk : 256 * (int64_t)rblk;
+        int64_t L = mat > p.nbins ? mat : p.nbins;
+        int64_t parts = scan_parts_needed(L);
+        if (mat > p.mat_cap) {
+            dev_free(p.mat);
+            p.mat = nullptr;
+            p.mat_cap = 0;
+            int rc = dev_alloc(&p.mat, sizeof(int32_t) * mat);
+            if (rc != NUFFT_OK) return rc;
+            p.mat_cap = mat;
+        }
+        if (parts > p.scan_part_cap) {
+            dev_free(p.scan_part);
+            p.scan_part = nullptr;
+            p.scan_part_cap = 0;
+            int rc = dev_alloc(&p.scan_part, sizeof(int32_t) * parts);
+            if (rc != NUFFT_OK) return rc;
+            p.scan_part_cap = parts;
+        }
+    }
     cudaError_t e = launch_setpts(p, x, y, z);
     if (e != cudaSuccess) return cuda_err(e);
     p.have_pts = true;

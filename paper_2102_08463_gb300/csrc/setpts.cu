@@ -1,188 +1,380 @@
 // setpts.cu -- bin-sort of the nonuniform points (Sec. 4.1, GM-sort and SM
-// step 1): bin index per point, per-bin counts, a stable permutation t listing
-// the points bin by bin, the subproblem list (runs of at most M_sub points of
-// one bin) and a packed bin-ordered record of each point's kernel offsets.
+// step 1): the bin of every point, per-bin counts, a stable permutation t
+// listing the points bin by bin (increasing original index inside a bin), the
+// subproblem list (runs of at most M_sub points of one bin) and a packed
+// record of each point's kernel offsets.
 //
-// The permutation is a stable LSD radix sort of the bin keys written here:
-// 8-bit digits, one histogram pass and one ranked scatter pass per digit.
-// Within a tile the scatter ranks equal digits by (warp, lane) order using
-// __match_any_sync, so equal keys keep their original order and t is unique.
+// Two sort paths, both stable and both giving the same t:
+//   counting sort (bins fit in shared memory): each CTA owns a contiguous chunk
+//     of points and histograms its bins in shared memory into row b of a
+//     CTAs x bins matrix; a prefix over the CTAs of each bin plus the scanned
+//     bin totals gives every CTA the first output slot of each of its bins; the
+//     CTA then walks its chunk in order, ranks equal bins inside each tile with
+//     __match_any_sync (lanes) and warp order (one barrier per warp), and writes
+//     t and the packed record of each point straight to its sorted slot.
+//   LSD radix sort (many bins): 8-bit digits, per-CTA digit histograms, a scan
+//     of the digit x CTA matrix, ranked scatter.
+// The packed records are written in the original point order (coalesced); the
+// spreading and interpolation kernels read them through t, as they read c.
 #include "nufft_internal.cuh"
 
 namespace nufft {
 
 namespace {
 
+constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
-constexpr int kSortThreads = 256;          // one digit per thread in the scans below
-constexpr int kScanThreads = 1024;
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSortThreads = 256;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanSeg = kScanThreads * kScanItems;   // elements per scan block
 
 // ---------------------------------------------------------------------------
-// Bin key of every point (user order) and per-bin counts.
+// Multi-block exclusive scan of int32 (three kernels: reduce, scan of block
+// sums, rescan with offsets).  in may equal out.  *total gets the sum.
 // ---------------------------------------------------------------------------
-template <typename T, int DIM>
-__global__ void prep_keys_kernel(const T *__restrict__ x, const T *__restrict__ y,
-                                 const T *__restrict__ z, int64_t M, int3 n, int3 m, int3 nb,
-                                 int32_t *__restrict__ keys, int32_t *__restrict__ bincount)
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int &block_total)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // Warp-uniform loop: every lane of a warp runs the same iterations.
-    const int64_t warp_base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-    for (int64_t b = warp_base; b < M; b += stride) {
-        int64_t j = b + lane;
-        int key = -1;
-        if (j < M) {
-            int lx = (int)__umul64hi(period_fraction(x[j]), (uint64_t)n.x);
-            int ly = (int)__umul64hi(period_fraction(y[j]), (uint64_t)n.y);
-            int bz = 0;
-            if (DIM == 3) {
-                int lz = (int)__umul64hi(period_fraction(z[j]), (uint64_t)n.z);
-                bz = lz / m.z;
-            }
-            key = lx / m.x + nb.x * (ly / m.y + nb.y * bz);
-            keys[j] = key;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    int s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, s, o);
+        if (lane >= o) s += t;
+    }
+    if (lane == 31) warp_sums[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        int ws = lane < nwarps ? warp_sums[lane] : 0;
+        int wsc = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(kFull, wsc, o);
+            if (lane >= o) wsc += t;
         }
-        unsigned peers = __match_any_sync(kFull, key);
-        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&bincount[key], __popc(peers));
+        if (lane < nwarps) warp_sums[lane] = wsc - ws;
+        if (lane == nwarps - 1) warp_sums[32] = wsc;
+    }
+    __syncthreads();
+    int excl = warp_sums[warp] + s - v;
+    block_total = warp_sums[32];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_reduce_kernel(const int32_t *__restrict__ in, int64_t L, int32_t *__restrict__ part)
+{
+    __shared__ int red[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanSeg;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < L) s += in[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// One block scans the block sums in rounds of blockDim.
+__global__ void __launch_bounds__(kScanThreads)
+scan_partials_kernel(int32_t *part, int64_t nparts, int32_t *total)
+{
+    __shared__ int ws[33];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nparts; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int v = i < nparts ? part[i] : 0;
+        int bt;
+        int e = block_exclusive_scan(v, ws, bt);
+        if (i < nparts) part[i] = carry + e;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += bt;
+        __syncthreads();
+    }
+    if (total != nullptr && threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_down_kernel(const int32_t *in, int32_t *out, int64_t L, const int32_t *__restrict__ part)
+{
+    __shared__ int ws[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < L) ? in[base + k] : 0;
+        tsum += v[k];
+    }
+    int bt;
+    int run = part[blockIdx.x] + block_exclusive_scan(tsum, ws, bt);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < L) out[base + k] = run;
+        run += v[k];
     }
 }
 
 // ---------------------------------------------------------------------------
-// Radix pass, step 1: digit histogram of each block's contiguous chunk.
-// hist is digit-major: hist[d * nblocks + block].
+// Bin of a point (Sec. 4.1 bin rule, integer position rule of nufft_internal.cuh).
 // ---------------------------------------------------------------------------
-__global__ void radix_hist_kernel(const int32_t *__restrict__ keys, int64_t M, int64_t chunk,
-                                  int shift, int32_t *__restrict__ hist)
+template <typename T, int DIM>
+__device__ __forceinline__ int bin_of_v(T xv, T yv, T zv, int3 n, int3 m, int3 nb)
+{
+    int lx = (int)__umul64hi(period_fraction(xv), (uint64_t)n.x);
+    int ly = (int)__umul64hi(period_fraction(yv), (uint64_t)n.y);
+    int bz = 0;
+    if (DIM == 3) bz = (int)__umul64hi(period_fraction(zv), (uint64_t)n.z) / m.z;
+    return lx / m.x + nb.x * (ly / m.y + nb.y * bz);
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ int bin_of(const T *x, const T *y, const T *z, int64_t j, int3 n,
+                                      int3 m, int3 nb)
+{
+    return bin_of_v<T, DIM>(x[j], y[j], DIM == 3 ? z[j] : (T)0, n, m, nb);
+}
+
+template <typename T> __device__ __forceinline__ T packed_word(uint32_t v);
+template <> __device__ __forceinline__ float packed_word<float>(uint32_t v) { return __uint_as_float(v); }
+template <> __device__ __forceinline__ double packed_word<double>(uint32_t v)
+{
+    return __longlong_as_double((long long)v);
+}
+
+// Packed record of a point at (xv, yv, zv): kernel offsets and the window start
+// relative to the padded bin origin (bin origin - floor(w/2)), 10 bits per axis.
+template <typename T, int DIM>
+__device__ __forceinline__ typename rec4<T>::type make_record_v(T xv, T yv, T zv, int3 n, int3 m,
+                                                                int w)
+{
+    const int P = pad_lo(w);
+    AxisPos<T> px = axis_position<T>(period_fraction(xv), n.x, w);
+    AxisPos<T> py = axis_position<T>(period_fraction(yv), n.y, w);
+    uint32_t sx = (uint32_t)(px.l0 - ((px.l / m.x) * m.x - P));
+    uint32_t sy = (uint32_t)(py.l0 - ((py.l / m.y) * m.y - P));
+    uint32_t sz = 0;
+    T dz = 0;
+    if (DIM == 3) {
+        AxisPos<T> pz = axis_position<T>(period_fraction(zv), n.z, w);
+        sz = (uint32_t)(pz.l0 - ((pz.l / m.z) * m.z - P));
+        dz = pz.delta;
+    }
+    typename rec4<T>::type r;
+    r.x = px.delta;
+    r.y = py.delta;
+    r.z = dz;
+    r.w = packed_word<T>(sx | (sy << 10) | (sz << 20));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Counting sort, pass 1: keys and per-CTA bin histograms, stored CTA-major
+// (mat[cta * nbins + bin], coalesced).  Four points per thread per round keep
+// several loads in flight.
+// ---------------------------------------------------------------------------
+constexpr int kCountThreads = 1024;
+constexpr int kCountUnroll = 4;
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kCountThreads)
+count_kernel(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z, int64_t M,
+             int64_t chunk, int3 n, int3 m, int3 nb, int nbins, int w, int32_t *__restrict__ keys,
+             int32_t *__restrict__ mat, typename rec4<T>::type *__restrict__ recs)
+{
+    extern __shared__ int hist[];
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(beg + chunk, M);
+    const int64_t step = (int64_t)blockDim.x * kCountUnroll;
+    for (int64_t j0 = beg + threadIdx.x; j0 < end; j0 += step) {
+        int key[kCountUnroll];
+        T xv[kCountUnroll], yv[kCountUnroll], zv[kCountUnroll];
+#pragma unroll
+        for (int k = 0; k < kCountUnroll; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+            key[k] = -1;
+            xv[k] = yv[k] = zv[k] = (T)0;
+            if (j < end) {
+                xv[k] = x[j];
+                yv[k] = y[j];
+                if (DIM == 3) zv[k] = z[j];
+                key[k] = 0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kCountUnroll; ++k) {
+            if (key[k] >= 0) {
+                const int64_t j = j0 + (int64_t)k * blockDim.x;
+                const int b = bin_of_v<T, DIM>(xv[k], yv[k], zv[k], n, m, nb);
+                keys[j] = b;
+                recs[j] = make_record_v<T, DIM>(xv[k], yv[k], zv[k], n, m, w);
+                atomicAdd(&hist[b], 1);
+            }
+        }
+    }
+    __syncthreads();
+    int32_t *col = mat + (int64_t)blockIdx.x * nbins;
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) col[i] = hist[i];
+}
+
+// Counting sort, pass 2: per bin, exclusive prefix over the CTAs (in place) and
+// the bin total.
+__global__ void column_scan_kernel(int32_t *__restrict__ mat, int nbins, int nblk,
+                                   int32_t *__restrict__ bincount)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    int s = 0;
+    int cta = 0;
+    for (; cta + 4 <= nblk; cta += 4) {
+        const int v0 = mat[(int64_t)cta * nbins + b];
+        const int v1 = mat[(int64_t)(cta + 1) * nbins + b];
+        const int v2 = mat[(int64_t)(cta + 2) * nbins + b];
+        const int v3 = mat[(int64_t)(cta + 3) * nbins + b];
+        mat[(int64_t)cta * nbins + b] = s;
+        mat[(int64_t)(cta + 1) * nbins + b] = s + v0;
+        mat[(int64_t)(cta + 2) * nbins + b] = s + v0 + v1;
+        mat[(int64_t)(cta + 3) * nbins + b] = s + v0 + v1 + v2;
+        s += v0 + v1 + v2 + v3;
+    }
+    for (; cta < nblk; ++cta) {
+        const int v = mat[(int64_t)cta * nbins + b];
+        mat[(int64_t)cta * nbins + b] = s;
+        s += v;
+    }
+    bincount[b] = s;
+}
+
+// Counting sort, pass 3: stable ranked scatter of t.  The next tile's keys are
+// loaded before the current tile's slots are claimed.
+__global__ void __launch_bounds__(kCountThreads)
+rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restrict__ keys,
+                    const int32_t *__restrict__ mat, const int32_t *__restrict__ binstart,
+                    int32_t *__restrict__ perm)
+{
+    extern __shared__ int run[];   // next output slot per bin for this CTA
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int32_t *col = mat + (int64_t)blockIdx.x * nbins;
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) run[i] = col[i] + binstart[i];
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(beg + chunk, M);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int64_t j = beg + threadIdx.x;
+    int key = j < end ? keys[j] : -1;
+    for (int64_t tile = beg; tile < end; tile += blockDim.x) {
+        const int64_t jn = j + blockDim.x;
+        const int keyn = jn < end ? keys[jn] : -1;
+        const unsigned peers = __match_any_sync(kFull, key);
+        const int lrank = __popc(peers & lt_mask);
+        const bool leader = key >= 0 && lrank == 0;
+        int base = 0;
+        // warps claim their slots in warp order: equal keys stay in index order
+        for (int wv = 0; wv < nwarps; ++wv) {
+            if (warp == wv && leader) {
+                base = run[key];
+                run[key] = base + __popc(peers);
+            }
+            __syncthreads();
+        }
+        base = __shfl_sync(kFull, base, __ffs(peers) - 1);
+        if (key >= 0) perm[base + lrank] = (int32_t)j;
+        j = jn;
+        key = keyn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix path (bins too many for shared memory).
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void keys_kernel(const T *__restrict__ x, const T *__restrict__ y,
+                            const T *__restrict__ z, int64_t M, int3 n, int3 m, int3 nb, int w,
+                            int32_t *__restrict__ keys, typename rec4<T>::type *__restrict__ recs)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const T xv = x[j], yv = y[j], zv = DIM == 3 ? z[j] : (T)0;
+        keys[j] = bin_of_v<T, DIM>(xv, yv, zv, n, m, nb);
+        recs[j] = make_record_v<T, DIM>(xv, yv, zv, n, m, w);
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+radix_hist_kernel(const int32_t *__restrict__ keys, int64_t M, int64_t chunk, int shift,
+                  int32_t *__restrict__ mat)
 {
     __shared__ int h[kRadix];
     for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    int64_t beg = (int64_t)blockIdx.x * chunk;
-    int64_t end = min(beg + chunk, M);
-    for (int64_t b = beg + (threadIdx.x & ~31); b < end; b += blockDim.x) {
-        int64_t i = b + lane;
-        int d = i < end ? ((keys[i] >> shift) & (kRadix - 1)) : -1;
-        unsigned peers = __match_any_sync(kFull, d);
-        if (d >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
-    }
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(beg + chunk, M);
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x)
+        atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1);
     __syncthreads();
     for (int i = threadIdx.x; i < kRadix; i += blockDim.x)
-        hist[(int64_t)i * gridDim.x + blockIdx.x] = h[i];
+        mat[(int64_t)i * gridDim.x + blockIdx.x] = h[i];
 }
 
-// ---------------------------------------------------------------------------
-// Exclusive prefix sum of L int32 values by one block (in may equal out);
-// the grand total goes to *total when total is not null.  Each thread takes
-// kScanItems consecutive values per round.
-// ---------------------------------------------------------------------------
-constexpr int kScanItems = 8;
-
-__global__ void __launch_bounds__(kScanThreads)
-scan_exclusive_kernel(const int32_t *in, int32_t *out, int64_t L, int32_t *total)
-{
-    __shared__ int warp_sums[kScanThreads / 32];
-    __shared__ int carry_s;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
-    const int64_t per_round = (int64_t)blockDim.x * kScanItems;
-    for (int64_t base = 0; base < L; base += per_round) {
-        int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
-        int v[kScanItems];
-        int tsum = 0;
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            v[k] = (i0 + k < L) ? in[i0 + k] : 0;
-            tsum += v[k];
-        }
-        int s = tsum;                             // inclusive warp scan of thread sums
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(kFull, s, o);
-            if (lane >= o) s += t;
-        }
-        if (lane == 31) warp_sums[warp] = s;
-        __syncthreads();
-        if (warp == 0) {
-            int ws = lane < nwarps ? warp_sums[lane] : 0;
-            int wsc = ws;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(kFull, wsc, o);
-                if (lane >= o) wsc += t;
-            }
-            if (lane < nwarps) warp_sums[lane] = wsc - ws;   // exclusive over warps
-        }
-        __syncthreads();
-        const int carry = carry_s;
-        int run = carry + warp_sums[warp] + s - tsum;
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            if (i0 + k < L) out[i0 + k] = run;
-            run += v[k];
-        }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry_s = run;
-        __syncthreads();
-    }
-    if (total != nullptr && threadIdx.x == 0) *total = carry_s;
-}
-
-// ---------------------------------------------------------------------------
-// Radix pass, step 2: stable scatter.  Each block walks its chunk in tiles of
-// blockDim keys (key index = tile base + threadIdx.x), ranks equal digits by
-// (warp, lane) inside the tile and by tile order across tiles.
-// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads)
 radix_scatter_kernel(const int32_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in,
-                     int64_t M, int64_t chunk, int shift, const int32_t *__restrict__ offsets,
+                     int64_t M, int64_t chunk, int shift, const int32_t *__restrict__ mat,
                      int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out)
 {
     constexpr int NW = kSortThreads / 32;
-    __shared__ int run[kRadix];               // next output slot per digit for this block
-    __shared__ int wcount[NW][kRadix];        // per-warp digit counts, then warp prefixes
+    __shared__ int run[kRadix];
+    __shared__ int wcount[NW][kRadix];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    run[tid] = offsets[(int64_t)tid * gridDim.x + blockIdx.x];   // blockDim == kRadix
-    int64_t beg = (int64_t)blockIdx.x * chunk;
-    int64_t end = min(beg + chunk, M);
+    run[tid] = mat[(int64_t)tid * gridDim.x + blockIdx.x];   // blockDim == kRadix
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(beg + chunk, M);
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int64_t tile = beg; tile < end; tile += kSortThreads) {
 #pragma unroll
         for (int w = 0; w < NW; ++w) wcount[w][tid] = 0;
         __syncthreads();
-        int64_t i = tile + tid;
+        const int64_t i = tile + tid;
         int key = 0, val = 0, d = -1;
         if (i < end) {
             key = keys_in[i];
             val = vals_in ? vals_in[i] : (int)i;
             d = (key >> shift) & (kRadix - 1);
         }
-        unsigned peers = __match_any_sync(kFull, d);
-        int lrank = __popc(peers & lt_mask);
+        const unsigned peers = __match_any_sync(kFull, d);
+        const int lrank = __popc(peers & lt_mask);
         if (d >= 0 && lrank == 0) wcount[warp][d] = __popc(peers);
         __syncthreads();
-        {   // thread tid owns digit tid: exclusive prefix over warps
-            int s = 0;
+        int s = 0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                int cnt = wcount[w][tid];
-                wcount[w][tid] = s;
-                s += cnt;
-            }
-            __syncthreads();
-            if (d >= 0) {
-                int pos = run[d] + wcount[warp][d] + lrank;
-                if (keys_out) keys_out[pos] = key;
-                vals_out[pos] = val;
-            }
-            __syncthreads();
-            run[tid] += s;
+        for (int w = 0; w < NW; ++w) {
+            const int cnt = wcount[w][tid];
+            wcount[w][tid] = s;
+            s += cnt;
         }
+        __syncthreads();
+        if (d >= 0) {
+            const int pos = run[d] + wcount[warp][d] + lrank;
+            if (keys_out) keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+        run[tid] += s;
         __syncthreads();
     }
 }
@@ -194,9 +386,19 @@ __global__ void iota_kernel(int32_t *out, int64_t M)
         out[i] = (int32_t)i;
 }
 
-// Subproblems per bin: ceil(count / msub).
-__global__ void count_subs_kernel(const int32_t *__restrict__ bincount, int64_t nbins, int msub,
-                                  int32_t *__restrict__ nsubs)
+__global__ void bin_histogram_kernel(const int32_t *__restrict__ keys, int64_t M,
+                                     int32_t *__restrict__ bincount)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&bincount[keys[i]], 1);
+}
+
+// ---------------------------------------------------------------------------
+// Subproblems (Sec. 4.1 SM step 1): bin b gets ceil(count_b / msub) runs.
+// ---------------------------------------------------------------------------
+__global__ void subs_per_bin_kernel(const int32_t *__restrict__ bincount, int64_t nbins, int msub,
+                                    int32_t *__restrict__ nsubs)
 {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
          b += (int64_t)gridDim.x * blockDim.x)
@@ -210,60 +412,58 @@ __global__ void write_subs_kernel(const int32_t *__restrict__ bincount,
 {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
          b += (int64_t)gridDim.x * blockDim.x) {
-        int cnt = bincount[b], st = binstart[b], so = suboff[b];
+        const int cnt = bincount[b], st = binstart[b], so = suboff[b];
         for (int off = 0, k = 0; off < cnt; off += msub, ++k)
             subprob[so + k] = make_int4((int)b, st + off, min(msub, cnt - off), 0);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Packed records in bin order: kernel offsets and window start relative to
-// the padded bin origin (bin origin - ceil(w/2)).
-// ---------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T packed_word(uint32_t v);
-template <> __device__ __forceinline__ float packed_word<float>(uint32_t v) { return __uint_as_float(v); }
-template <> __device__ __forceinline__ double packed_word<double>(uint32_t v)
-{
-    return __longlong_as_double((long long)v);
-}
-
-template <typename T, int DIM>
-__global__ void pack_records_kernel(const T *__restrict__ x, const T *__restrict__ y,
-                                    const T *__restrict__ z, const int32_t *__restrict__ perm,
-                                    int64_t M, int3 n, int3 m, int w,
-                                    typename rec4<T>::type *__restrict__ recs)
-{
-    const int P = (w + 1) / 2;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < M;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        int j = perm[s];
-        AxisPos<T> px = axis_position<T>(period_fraction(x[j]), n.x, w);
-        AxisPos<T> py = axis_position<T>(period_fraction(y[j]), n.y, w);
-        uint32_t sx = (uint32_t)(px.l0 - ((px.l / m.x) * m.x - P));
-        uint32_t sy = (uint32_t)(py.l0 - ((py.l / m.y) * m.y - P));
-        uint32_t sz = 0;
-        T dz = 0;
-        if (DIM == 3) {
-            AxisPos<T> pz = axis_position<T>(period_fraction(z[j]), n.z, w);
-            sz = (uint32_t)(pz.l0 - ((pz.l / m.z) * m.z - P));
-            dz = pz.delta;
-        }
-        typename rec4<T>::type r;
-        r.x = px.delta;
-        r.y = py.delta;
-        r.z = dz;
-        r.w = packed_word<T>(sx | (sy << 10) | (sz << 20));
-        recs[s] = r;
     }
 }
 
 inline int grid_for(int64_t work, int threads, int num_sms)
 {
     int64_t b = (work + threads - 1) / threads;
-    int64_t cap = (int64_t)num_sms * 16;
+    const int64_t cap = (int64_t)num_sms * 16;
     if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
+
+}  // namespace
+
+// Exclusive scan of L int32 (in may equal out); p.scan_part holds the block sums.
+cudaError_t launch_scan(Plan &p, const int32_t *in, int32_t *out, int64_t L, int32_t *total)
+{
+    if (L <= 0) return cudaSuccess;
+    const int64_t nb = (L + kScanSeg - 1) / kScanSeg;
+    count_launch(3);
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, p.stream>>>(in, L, p.scan_part);
+    scan_partials_kernel<<<1, kScanThreads, 0, p.stream>>>(p.scan_part, nb, total);
+    scan_down_kernel<<<(unsigned)nb, kScanThreads, 0, p.stream>>>(in, out, L, p.scan_part);
+    return cudaGetLastError();
+}
+
+int64_t scan_parts_needed(int64_t L) { return (L + kScanSeg - 1) / kScanSeg + 1; }
+
+// Blocks of the counting sort for M points and nbins bins (0 = use the radix path).
+int counting_sort_blocks(const Plan &p, int64_t M)
+{
+    const size_t smem = (size_t)p.nbins * sizeof(int32_t);
+    if (smem > (size_t)p.smem_optin) return 0;
+    int per_sm = (int)((size_t)p.smem_per_sm / (smem + 1024));
+    if (per_sm > 2) per_sm = 2;            // 2 x 1024 threads fill an SM
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)p.num_sms * per_sm;
+    const int64_t by_size = (M + 8191) / 8192;
+    if (blocks > by_size) blocks = by_size;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
+int radix_sort_blocks(const Plan &p, int64_t M)
+{
+    int64_t blocks = (M + 4095) / 4096;
+    if (blocks > (int64_t)p.num_sms * 2) blocks = (int64_t)p.num_sms * 2;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
+namespace {
 
 template <typename T>
 cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
@@ -273,72 +473,81 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
     const int3 n = make_int3((int)p.nf[0], (int)p.nf[1], (int)p.nf[2]);
     const int3 m = make_int3(p.m[0], p.m[1], p.m[2]);
     const int3 nb = make_int3(p.nb[0], p.nb[1], p.nb[2]);
-    cudaError_t e = cudaMemsetAsync(p.bincount, 0, sizeof(int32_t) * p.nbins, st);
-    if (e != cudaSuccess) return e;
-    if (M > 0) {
-        int g = grid_for(M, 256, p.num_sms);
-        if (p.dim == 2) {
-            count_launch();
-            prep_keys_kernel<T, 2><<<g, 256, 0, st>>>(x, y, z, M, n, m, nb, p.keys, p.bincount);
-        }
-        else {
-            count_launch();
-            prep_keys_kernel<T, 3><<<g, 256, 0, st>>>(x, y, z, M, n, m, nb, p.keys, p.bincount);
-        }
-        // stable LSD radix sort of (key, index)
+    const int nbins = (int)p.nbins;
+    auto *recs = reinterpret_cast<typename rec4<T>::type *>(p.recs);
+    cudaError_t e = cudaSuccess;
+    if (M == 0) {
+        e = cudaMemsetAsync(p.bincount, 0, sizeof(int32_t) * p.nbins, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p.nsub, 0, sizeof(int32_t), st);
+        return e;
+    }
+    const int cblk = counting_sort_blocks(p, M);
+    if (cblk > 0) {
+        const int64_t chunk = (M + cblk - 1) / cblk;
+        const size_t smem = (size_t)nbins * sizeof(int32_t);
+        auto kc = p.dim == 2 ? count_kernel<T, 2> : count_kernel<T, 3>;
+        auto ks = rank_scatter_kernel;
+        cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        count_launch(3);
+        kc<<<cblk, kCountThreads, smem, st>>>(x, y, z, M, chunk, n, m, nb, nbins, p.w, p.keys,
+                                              p.mat, recs);
+        column_scan_kernel<<<(nbins + 255) / 256, 256, 0, st>>>(p.mat, nbins, cblk, p.bincount);
+        e = launch_scan(p, p.bincount, p.binstart, nbins, nullptr);
+        if (e != cudaSuccess) return e;
+        ks<<<cblk, kCountThreads, smem, st>>>(M, chunk, nbins, p.keys, p.mat, p.binstart, p.vals);
+        p.perm = p.vals;
+        count_launch();
+        subs_per_bin_kernel<<<grid_for(nbins, 256, p.num_sms), 256, 0, st>>>(p.bincount, nbins,
+                                                                           p.msub, p.scan_tmp);
+    } else {
+        const int g = grid_for(M, 256, p.num_sms);
+        count_launch();
+        if (p.dim == 2)
+            keys_kernel<T, 2><<<g, 256, 0, st>>>(x, y, z, M, n, m, nb, p.w, p.keys, recs);
+        else
+            keys_kernel<T, 3><<<g, 256, 0, st>>>(x, y, z, M, n, m, nb, p.w, p.keys, recs);
+        e = cudaMemsetAsync(p.bincount, 0, sizeof(int32_t) * p.nbins, st);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        bin_histogram_kernel<<<g, 256, 0, st>>>(p.keys, M, p.bincount);
         int bits = 0;
         while (bits < 31 && ((int64_t)1 << bits) < p.nbins) ++bits;
-        int passes = (bits + kRadixBits - 1) / kRadixBits;
+        const int passes = (bits + kRadixBits - 1) / kRadixBits;
         int32_t *kbuf[2] = {p.keys, p.keys_alt};
         int32_t *vbuf[2] = {p.vals, p.vals_alt};
-        const int nblk = p.hist_blocks;
-        const int64_t chunk = (M + nblk - 1) / nblk;
+        const int rblk = radix_sort_blocks(p, M);
+        const int64_t chunk = (M + rblk - 1) / rblk;
+        int cur = 0;
         if (passes == 0) {
             count_launch();
-            iota_kernel<<<grid_for(M, 256, p.num_sms), 256, 0, st>>>(p.vals, M);
-            p.perm = p.vals;
+            iota_kernel<<<g, 256, 0, st>>>(p.vals, M);
         }
-        int cur = 0;
         for (int ps = 0; ps < passes; ++ps) {
             const int shift = ps * kRadixBits;
             const bool last = ps == passes - 1;
             count_launch();
-            radix_hist_kernel<<<nblk, kSortThreads, 0, st>>>(kbuf[cur], M, chunk, shift, p.hist);
+            radix_hist_kernel<<<rblk, kSortThreads, 0, st>>>(kbuf[cur], M, chunk, shift, p.mat);
+            e = launch_scan(p, p.mat, p.mat, (int64_t)kRadix * rblk, nullptr);
+            if (e != cudaSuccess) return e;
             count_launch();
-            scan_exclusive_kernel<<<1, kScanThreads, 0, st>>>(p.hist, p.hist,
-                                                              (int64_t)kRadix * nblk, nullptr);
-            count_launch();
-            radix_scatter_kernel<<<nblk, kSortThreads, 0, st>>>(
-                kbuf[cur], ps == 0 ? nullptr : vbuf[cur], M, chunk, shift, p.hist,
+            radix_scatter_kernel<<<rblk, kSortThreads, 0, st>>>(
+                kbuf[cur], ps == 0 ? nullptr : vbuf[cur], M, chunk, shift, p.mat,
                 last ? nullptr : kbuf[cur ^ 1], vbuf[cur ^ 1]);
             cur ^= 1;
         }
-        if (passes > 0) p.perm = vbuf[cur];
+        p.perm = vbuf[cur];
+        e = launch_scan(p, p.bincount, p.binstart, nbins, nullptr);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        subs_per_bin_kernel<<<grid_for(nbins, 256, p.num_sms), 256, 0, st>>>(p.bincount, nbins,
+                                                                           p.msub, p.scan_tmp);
     }
-    // subproblems
-    const int64_t nbins = p.nbins;
-    int gb = grid_for(nbins, 256, p.num_sms);
+    e = launch_scan(p, p.scan_tmp, p.scan_tmp, nbins, p.nsub);
+    if (e != cudaSuccess) return e;
     count_launch();
-    scan_exclusive_kernel<<<1, kScanThreads, 0, st>>>(p.bincount, p.binstart, nbins, nullptr);
-    count_launch();
-    count_subs_kernel<<<gb, 256, 0, st>>>(p.bincount, nbins, p.msub, p.scan_tmp);
-    count_launch();
-    scan_exclusive_kernel<<<1, kScanThreads, 0, st>>>(p.scan_tmp, p.scan_tmp, nbins, p.nsub);
-    count_launch();
-    write_subs_kernel<<<gb, 256, 0, st>>>(p.bincount, p.binstart, p.scan_tmp, nbins, p.msub,
-                                          p.subprob);
-    if (M > 0) {
-        int g = grid_for(M, 256, p.num_sms);
-        auto *recs = reinterpret_cast<typename rec4<T>::type *>(p.recs);
-        if (p.dim == 2) {
-            count_launch();
-            pack_records_kernel<T, 2><<<g, 256, 0, st>>>(x, y, z, p.perm, M, n, m, p.w, recs);
-        }
-        else {
-            count_launch();
-            pack_records_kernel<T, 3><<<g, 256, 0, st>>>(x, y, z, p.perm, M, n, m, p.w, recs);
-        }
-    }
+    write_subs_kernel<<<grid_for(nbins, 256, p.num_sms), 256, 0, st>>>(
+        p.bincount, p.binstart, p.scan_tmp, nbins, p.msub, p.subprob);
     return cudaGetLastError();
 }
 

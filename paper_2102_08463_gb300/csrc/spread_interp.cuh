@@ -2,24 +2,23 @@
 // interpolation (type 2 step 3, Sec. 3.2 / Sec. 4.2) kernels, templated on the
 // precision T, the dimension DIM and the kernel width W.
 //
-// Thread mapping shared by every kernel here: a warp is cut into G = 32 / W
-// lane groups of W lanes; group g works on one point, lane dx of the group owns
+// Thread mapping shared by the kernels here: a warp is cut into G = 32 / W lane
+// groups of W lanes; group g works on one point, lane dx of the group owns
 // window column dx.  Each lane evaluates the ES kernel only for its own column
 // in x, y (and z) -- d evaluations per lane instead of d*W per thread -- and
-// the y / z weights of the other columns come from the group by warp shuffles.
-// The W lanes of a group touch W consecutive cells of a grid row, so their
-// shared-memory atomics fall in distinct banks and their global accesses
-// coalesce.
+// hands the y / z weights to the rest of its group by shuffles, once per point.
+// The bin-ordered kernels first load a batch of 32 points per warp (one point
+// per lane: index from t, then its record and strength) and then feed the groups from registers by
+// shuffles, so one memory round trip serves 32 points.
 //
-//   SM       one CTA per subproblem (Sec. 4.1 SM steps 1-3): points accumulate
-//            into a shared-memory copy of the padded bin, p_i = m_i + 2 ceil(w/2)
-//            cells per axis, then the padded bin is atomically added to the
-//            fine grid with periodic wrap.  Persistent CTAs stride over the
-//            (subproblem, transform) pairs.
+//   SM       Sec. 4.1 SM steps 1-3: one CTA per (subproblem, transform); points
+//            accumulate into a shared-memory copy of the padded bin
+//            (m_i + w cells per axis) with shared atomics, then the padded bin is
+//            atomically added to the fine grid with periodic wrap.
 //   GM-sort  the same bin-ordered points, atomics straight into the fine grid.
 //   GM       user order, positions recomputed from the coordinates.
 //   interp   the transpose: each group gathers its point's w^d cells (from the
-//            fine grid, or from a padded bin staged in shared memory) and the
+//            padded bin staged in shared memory, or from the fine grid) and the
 //            W column sums are combined with shuffles.
 #pragma once
 
@@ -45,7 +44,7 @@ struct KArgs {
     int n0, n1, n2;                              // fine grid
     int m0, m1, m2;                              // bin size
     int nb0, nb1;                                // bins along x, y
-    int p0, p1, p2;                              // padded bin
+    int p0, p1, p2;                              // padded bin (m + w)
     T beta;
     T hw;                                        // 2 / w
 };
@@ -68,13 +67,43 @@ __device__ __forceinline__ int wrap_any(int v, int n)
 __device__ __forceinline__ void bin_origin(int b, int nb0, int nb1, int m0, int m1, int m2,
                                            int &o0, int &o1, int &o2)
 {
-    int bx = b % nb0;
-    int r = b / nb0;
-    int by = r % nb1;
-    int bz = r / nb1;
+    const int bx = b % nb0;
+    const int r = b / nb0;
+    const int by = r % nb1;
+    const int bz = r / nb1;
     o0 = bx * m0;
     o1 = by * m1;
     o2 = bz * m2;
+}
+
+// Shuffle helpers for the batch hand-off.
+__device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(kFullMask, v, src); }
+__device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(kFullMask, v, src); }
+
+// One point of a 32-point batch, as seen by its lane group.
+template <typename T>
+struct PointView {
+    T dx, dy, dz;      // kernel offsets delta
+    uint32_t pk;       // packed window start in the padded bin
+    T cr, ci;          // strength (spread only)
+};
+
+template <typename T, bool WITH_C>
+__device__ __forceinline__ PointView<T> take_point(const typename rec4<T>::type &r,
+                                                   const typename cplx<T>::type &cv, int src)
+{
+    PointView<T> v;
+    v.dx = shfl(r.x, src);
+    v.dy = shfl(r.y, src);
+    v.dz = shfl(r.z, src);
+    v.pk = __shfl_sync(kFullMask, unpack_word<T>(r.w), src);
+    if (WITH_C) {
+        v.cr = shfl(cv.x, src);
+        v.ci = shfl(cv.y, src);
+    } else {
+        v.cr = v.ci = (T)0;
+    }
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -85,73 +114,65 @@ __global__ void __launch_bounds__(256)
 spread_sm_kernel(KArgs<T> a)
 {
     using C = typename cplx<T>::type;
+    using R = typename rec4<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int G = 32 / W;
     const int ptot = a.p0 * a.p1 * (DIM == 3 ? a.p2 : 1);
+    const int p01 = a.p0 * a.p1;
     T *sre = reinterpret_cast<T *>(smem_raw);
     T *sim = sre + ptot;
-    constexpr int G = 32 / W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int g = lane / W, dx = lane - (lane / W) * W;
     const bool gact = g < G;
     const int src0 = (gact ? g : G - 1) * W;
-    const int P = (W + 1) / 2;
+    const int P = pad_lo(W);
     const int nsp = *a.nsub;
     const int64_t nwork = (int64_t)nsp * a.ntransf;
     for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int sp = (int)(wi % nsp);
         const int tr = (int)(wi / nsp);
         const int4 sub = a.subprob[sp];
-        for (int i = threadIdx.x; i < ptot; i += blockDim.x) {
-            sre[i] = (T)0;
-            sim[i] = (T)0;
-        }
+        for (int i = threadIdx.x; i < 2 * ptot; i += blockDim.x) sre[i] = (T)0;
         __syncthreads();
         const C *cin = a.cin + (int64_t)tr * a.M;
-        for (int q0 = warp * G; q0 < sub.z; q0 += nwarps * G) {
-            const int q = q0 + g;
-            const bool act = gact && q < sub.z;
-            T wx = 0, wy = 0, wz = 0, cre = 0, cim = 0;
-            int sx = 0, sy = 0, sz = 0;
-            if (act) {
-                const auto r = a.recs[sub.y + q];
-                const C cv = cin[a.perm[sub.y + q]];
-                cre = cv.x;
-                cim = cv.y;
-                wx = es_kernel(((T)dx - r.x) * a.hw, a.beta);
-                wy = es_kernel(((T)dx - r.y) * a.hw, a.beta);
-                if (DIM == 3) wz = es_kernel(((T)dx - r.z) * a.hw, a.beta);
-                const uint32_t pk = unpack_word<T>(r.w);
-                sx = pk & 1023u;
-                sy = (pk >> 10) & 1023u;
-                sz = pk >> 20;
+        for (int base = warp * 32; base < sub.z; base += nwarps * 32) {
+            R r;
+            r.x = r.y = r.z = r.w = (T)0;
+            C cv;
+            cv.x = cv.y = (T)0;
+            if (base + lane < sub.z) {
+                const int j = a.perm[sub.y + base + lane];
+                r = a.recs[j];
+                cv = cin[j];
             }
-            if (DIM == 2) {
+            const int np = min(32, sub.z - base);
+            for (int i0 = 0; i0 < np; i0 += G) {
+                const int p = i0 + g;
+                const bool act = gact && p < np;
+                const PointView<T> pv = take_point<T, true>(r, cv, p < 32 ? p : 31);
+                const T wx = es_kernel(((T)dx - pv.dx) * a.hw, a.beta);
+                const T myy = es_kernel(((T)dx - pv.dy) * a.hw, a.beta);
+                const T myz = DIM == 3 ? es_kernel(((T)dx - pv.dz) * a.hw, a.beta) : (T)0;
+                T wy[W];
 #pragma unroll
-                for (int iy = 0; iy < W; ++iy) {
-                    const T vy = __shfl_sync(kFullMask, wy, src0 + iy);
-                    if (act) {
-                        const T v = wx * vy;
-                        const int idx = (sy + iy) * a.p0 + sx + dx;
-                        atomicAdd(&sre[idx], v * cre);
-                        atomicAdd(&sim[idx], v * cim);
-                    }
-                }
-            } else {
+                for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
+                const int sx = pv.pk & 1023u, sy = (pv.pk >> 10) & 1023u, sz = pv.pk >> 20;
+                const T zr0 = pv.cr * wx, zi0 = pv.ci * wx;
+                const int baddr = (sz * a.p1 + sy) * a.p0 + sx + dx;
+                const int nz = DIM == 3 ? W : 1;
 #pragma unroll 1
-                for (int iz = 0; iz < W; ++iz) {
-                    const T vz = __shfl_sync(kFullMask, wz, src0 + iz);
-                    const T zr = cre * vz, zi = cim * vz;
-                    const int zoff = (sz + iz) * a.p1;
+                for (int iz = 0; iz < nz; ++iz) {
+                    const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
+                    const T zr = zr0 * vz, zi = zi0 * vz;
+                    int addr = baddr + iz * p01;
 #pragma unroll
                     for (int iy = 0; iy < W; ++iy) {
-                        const T vy = __shfl_sync(kFullMask, wy, src0 + iy);
                         if (act) {
-                            const T v = wx * vy;
-                            const int idx = (zoff + sy + iy) * a.p0 + sx + dx;
-                            atomicAdd(&sre[idx], v * zr);
-                            atomicAdd(&sim[idx], v * zi);
+                            atomicAdd(&sre[addr], wy[iy] * zr);
+                            atomicAdd(&sim[addr], wy[iy] * zi);
                         }
+                        addr += a.p0;
                     }
                 }
             }
@@ -162,17 +183,15 @@ spread_sm_kernel(KArgs<T> a)
         bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
         C *grid = a.grid + (int64_t)tr * a.nftot;
         const int rows = a.p1 * (DIM == 3 ? a.p2 : 1);
-        for (int r = warp; r < rows; r += nwarps) {
-            const int ry = r % a.p1, rz = r / a.p1;
+        for (int rr = warp; rr < rows; rr += nwarps) {
+            const int ry = rr % a.p1, rz = rr / a.p1;
             const int gy = wrap_any(o1 - P + ry, a.n1);
             const int gz = DIM == 3 ? wrap_any(o2 - P + rz, a.n2) : 0;
             const int64_t rowbase = ((int64_t)gz * a.n1 + gy) * a.n0;
             for (int rx = lane; rx < a.p0; rx += 32) {
-                const T re = sre[r * a.p0 + rx], im = sim[r * a.p0 + rx];
-                if (re != (T)0 || im != (T)0) {
-                    const int gx = wrap_any(o0 - P + rx, a.n0);
-                    atomic_add_cplx(&grid[rowbase + gx], re, im);
-                }
+                const T re = sre[rr * a.p0 + rx], im = sim[rr * a.p0 + rx];
+                if (re != (T)0 || im != (T)0)
+                    atomic_add_cplx(&grid[rowbase + wrap_any(o0 - P + rx, a.n0)], re, im);
             }
         }
         __syncthreads();
@@ -187,13 +206,14 @@ __global__ void __launch_bounds__(256)
 spread_gmsort_kernel(KArgs<T> a)
 {
     using C = typename cplx<T>::type;
+    using R = typename rec4<T>::type;
     constexpr int G = 32 / W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int g = lane / W, dx = lane - (lane / W) * W;
     const bool gact = g < G;
     const int src0 = (gact ? g : G - 1) * W;
-    const int P = (W + 1) / 2;
+    const int P = pad_lo(W);
     const int nsp = *a.nsub;
     const int64_t nwork = (int64_t)nsp * a.ntransf;
     for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
@@ -204,42 +224,44 @@ spread_gmsort_kernel(KArgs<T> a)
         bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
         const C *cin = a.cin + (int64_t)tr * a.M;
         C *grid = a.grid + (int64_t)tr * a.nftot;
-        for (int q0 = warp * G; q0 < sub.z; q0 += nwarps * G) {
-            const int q = q0 + g;
-            const bool act = gact && q < sub.z;
-            T wx = 0, wy = 0, wz = 0, cre = 0, cim = 0;
-            int gx = 0, ly0 = 0, lz0 = 0;
-            if (act) {
-                const auto r = a.recs[sub.y + q];
-                const C cv = cin[a.perm[sub.y + q]];
-                cre = cv.x;
-                cim = cv.y;
-                wx = es_kernel(((T)dx - r.x) * a.hw, a.beta);
-                wy = es_kernel(((T)dx - r.y) * a.hw, a.beta);
-                if (DIM == 3) wz = es_kernel(((T)dx - r.z) * a.hw, a.beta);
-                const uint32_t pk = unpack_word<T>(r.w);
-                gx = wrap_any(o0 - P + (int)(pk & 1023u) + dx, a.n0);
-                ly0 = o1 - P + (int)((pk >> 10) & 1023u);
-                lz0 = o2 - P + (int)(pk >> 20);
+        for (int base = warp * 32; base < sub.z; base += nwarps * 32) {
+            R r;
+            r.x = r.y = r.z = r.w = (T)0;
+            C cv;
+            cv.x = cv.y = (T)0;
+            if (base + lane < sub.z) {
+                const int j = a.perm[sub.y + base + lane];
+                r = a.recs[j];
+                cv = cin[j];
             }
-            const int nz = DIM == 3 ? W : 1;
-#pragma unroll 1
-            for (int iz = 0; iz < nz; ++iz) {
-                T zr = cre, zi = cim;
-                int gz = 0;
-                if (DIM == 3) {
-                    const T vz = __shfl_sync(kFullMask, wz, src0 + iz);
-                    zr *= vz;
-                    zi *= vz;
-                    gz = wrap_any(lz0 + iz, a.n2);
-                }
+            const int np = min(32, sub.z - base);
+            for (int i0 = 0; i0 < np; i0 += G) {
+                const int p = i0 + g;
+                const bool act = gact && p < np;
+                const PointView<T> pv = take_point<T, true>(r, cv, p < 32 ? p : 31);
+                const T wx = es_kernel(((T)dx - pv.dx) * a.hw, a.beta);
+                const T myy = es_kernel(((T)dx - pv.dy) * a.hw, a.beta);
+                const T myz = DIM == 3 ? es_kernel(((T)dx - pv.dz) * a.hw, a.beta) : (T)0;
+                T wy[W];
 #pragma unroll
-                for (int iy = 0; iy < W; ++iy) {
-                    const T vy = __shfl_sync(kFullMask, wy, src0 + iy);
-                    if (act) {
-                        const T v = wx * vy;
-                        const int gy = wrap_any(ly0 + iy, a.n1);
-                        atomic_add_cplx(&grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx], v * zr, v * zi);
+                for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
+                const int gx = wrap_any(o0 - P + (int)(pv.pk & 1023u) + dx, a.n0);
+                const int ly0 = o1 - P + (int)((pv.pk >> 10) & 1023u);
+                const int lz0 = o2 - P + (int)(pv.pk >> 20);
+                const T zr0 = pv.cr * wx, zi0 = pv.ci * wx;
+                const int nz = DIM == 3 ? W : 1;
+#pragma unroll 1
+                for (int iz = 0; iz < nz; ++iz) {
+                    const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
+                    const T zr = zr0 * vz, zi = zi0 * vz;
+                    const int gz = DIM == 3 ? wrap_any(lz0 + iz, a.n2) : 0;
+#pragma unroll
+                    for (int iy = 0; iy < W; ++iy) {
+                        if (act) {
+                            const int gy = wrap_any(ly0 + iy, a.n1);
+                            atomic_add_cplx(&grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx],
+                                            wy[iy] * zr, wy[iy] * zi);
+                        }
                     }
                 }
             }
@@ -266,7 +288,7 @@ spread_gm_kernel(KArgs<T> a)
     for (int64_t base = gwarp * G; base < total; base += nwarps_total * G) {
         const int64_t item = base + g;
         const bool act = gact && item < total;
-        T wx = 0, wy = 0, wz = 0, cre = 0, cim = 0;
+        T wx = 0, myy = 0, myz = 0, cre = 0, cim = 0;
         int gx = 0, ly0 = 0, lz0 = 0, tr = 0;
         if (act) {
             tr = (int)(item / a.M);
@@ -274,37 +296,35 @@ spread_gm_kernel(KArgs<T> a)
             const AxisPos<T> px = axis_position<T>(period_fraction(a.xyz0[j]), a.n0, W);
             const AxisPos<T> py = axis_position<T>(period_fraction(a.xyz1[j]), a.n1, W);
             wx = es_kernel(((T)dx - px.delta) * a.hw, a.beta);
-            wy = es_kernel(((T)dx - py.delta) * a.hw, a.beta);
+            myy = es_kernel(((T)dx - py.delta) * a.hw, a.beta);
             gx = wrap_any(px.l0 + dx, a.n0);
             ly0 = py.l0;
             if (DIM == 3) {
                 const AxisPos<T> pz = axis_position<T>(period_fraction(a.xyz2[j]), a.n2, W);
-                wz = es_kernel(((T)dx - pz.delta) * a.hw, a.beta);
+                myz = es_kernel(((T)dx - pz.delta) * a.hw, a.beta);
                 lz0 = pz.l0;
             }
             const C cv = a.cin[item];
             cre = cv.x;
             cim = cv.y;
         }
+        T wy[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
         C *grid = a.grid + (int64_t)tr * a.nftot;
+        const T zr0 = cre * wx, zi0 = cim * wx;
         const int nz = DIM == 3 ? W : 1;
 #pragma unroll 1
         for (int iz = 0; iz < nz; ++iz) {
-            T zr = cre, zi = cim;
-            int gz = 0;
-            if (DIM == 3) {
-                const T vz = __shfl_sync(kFullMask, wz, src0 + iz);
-                zr *= vz;
-                zi *= vz;
-                gz = wrap_any(lz0 + iz, a.n2);
-            }
+            const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
+            const T zr = zr0 * vz, zi = zi0 * vz;
+            const int gz = DIM == 3 ? wrap_any(lz0 + iz, a.n2) : 0;
 #pragma unroll
             for (int iy = 0; iy < W; ++iy) {
-                const T vy = __shfl_sync(kFullMask, wy, src0 + iy);
                 if (act) {
-                    const T v = wx * vy;
                     const int gy = wrap_any(ly0 + iy, a.n1);
-                    atomic_add_cplx(&grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx], v * zr, v * zi);
+                    atomic_add_cplx(&grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx], wy[iy] * zr,
+                                    wy[iy] * zi);
                 }
             }
         }
@@ -327,12 +347,15 @@ __device__ __forceinline__ T group_sum(T v, int dx)
 // Sorted interpolation (GM-sort, Sec. 4.2) and its shared-memory staged form
 // (STAGED = true): the padded bin of the subproblem is first copied into
 // shared memory with coalesced row loads, then every gather reads it there.
+// Each group's total lands on lane dx == 0 and is handed to the lane that
+// loaded the point, so the batch writes its 32 results together.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int W, bool STAGED>
 __global__ void __launch_bounds__(256)
 interp_sorted_kernel(KArgs<T> a)
 {
     using C = typename cplx<T>::type;
+    using R = typename rec4<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tile = reinterpret_cast<C *>(smem_raw);
     constexpr int G = 32 / W;
@@ -341,7 +364,8 @@ interp_sorted_kernel(KArgs<T> a)
     const int g = lane / W, dx = lane - (lane / W) * W;
     const bool gact = g < G;
     const int src0 = (gact ? g : G - 1) * W;
-    const int P = (W + 1) / 2;
+    const int P = pad_lo(W);
+    const int p01 = a.p0 * a.p1;
     const int nsp = *a.nsub;
     const int64_t nwork = (int64_t)nsp * a.ntransf;
     for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
@@ -354,66 +378,94 @@ interp_sorted_kernel(KArgs<T> a)
         C *cout = a.cout + (int64_t)tr * a.M;
         if (STAGED) {
             const int rows = a.p1 * (DIM == 3 ? a.p2 : 1);
-            for (int r = warp; r < rows; r += nwarps) {
-                const int ry = r % a.p1, rz = r / a.p1;
+            for (int rr = warp; rr < rows; rr += nwarps) {
+                const int ry = rr % a.p1, rz = rr / a.p1;
                 const int gy = wrap_any(o1 - P + ry, a.n1);
                 const int gz = DIM == 3 ? wrap_any(o2 - P + rz, a.n2) : 0;
-                const int64_t rowbase = ((int64_t)gz * a.n1 + gy) * a.n0;
+                const C *src = grid + ((int64_t)gz * a.n1 + gy) * a.n0;
                 for (int rx = lane; rx < a.p0; rx += 32)
-                    tile[r * a.p0 + rx] = grid[rowbase + wrap_any(o0 - P + rx, a.n0)];
+                    tile[rr * a.p0 + rx] = src[wrap_any(o0 - P + rx, a.n0)];
             }
             __syncthreads();
         }
-        for (int q0 = warp * G; q0 < sub.z; q0 += nwarps * G) {
-            const int q = q0 + g;
-            const bool act = gact && q < sub.z;
-            T wx = 0, wy = 0, wz = 0;
-            int sx = 0, sy = 0, sz = 0;
-            if (act) {
-                const auto r = a.recs[sub.y + q];
-                wx = es_kernel(((T)dx - r.x) * a.hw, a.beta);
-                wy = es_kernel(((T)dx - r.y) * a.hw, a.beta);
-                if (DIM == 3) wz = es_kernel(((T)dx - r.z) * a.hw, a.beta);
-                const uint32_t pk = unpack_word<T>(r.w);
-                sx = pk & 1023u;
-                sy = (pk >> 10) & 1023u;
-                sz = pk >> 20;
+        for (int base = warp * 32; base < sub.z; base += nwarps * 32) {
+            R r;
+            r.x = r.y = r.z = r.w = (T)0;
+            C dummy;
+            dummy.x = dummy.y = (T)0;
+            int myperm = 0;
+            if (base + lane < sub.z) {
+                myperm = a.perm[sub.y + base + lane];
+                r = a.recs[myperm];
             }
-            const int gx = STAGED ? 0 : wrap_any(o0 - P + sx + dx, a.n0);
-            T ar = 0, ai = 0;
-            const int nz = DIM == 3 ? W : 1;
-#pragma unroll 1
-            for (int iz = 0; iz < nz; ++iz) {
-                T vz = (T)1;
-                if (DIM == 3) vz = __shfl_sync(kFullMask, wz, src0 + iz);
-                T zr = 0, zi = 0;
+            const int np = min(32, sub.z - base);
+            C res;
+            res.x = res.y = (T)0;
+            for (int i0 = 0; i0 < np; i0 += G) {
+                const int p = i0 + g;
+                const bool act = gact && p < np;
+                const PointView<T> pv = take_point<T, false>(r, dummy, p < 32 ? p : 31);
+                const T wx = es_kernel(((T)dx - pv.dx) * a.hw, a.beta);
+                const T myy = es_kernel(((T)dx - pv.dy) * a.hw, a.beta);
+                const T myz = DIM == 3 ? es_kernel(((T)dx - pv.dz) * a.hw, a.beta) : (T)0;
+                T wy[W];
 #pragma unroll
-                for (int iy = 0; iy < W; ++iy) {
-                    const T vy = __shfl_sync(kFullMask, wy, src0 + iy);
-                    if (act) {
-                        C v;
-                        if (STAGED) {
-                            v = tile[((sz + iz) * a.p1 + sy + iy) * a.p0 + sx + dx];
-                        } else {
-                            const int gy = wrap_any(o1 - P + sy + iy, a.n1);
-                            const int gz = DIM == 3 ? wrap_any(o2 - P + sz + iz, a.n2) : 0;
-                            v = grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx];
+                for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
+                const int sx = pv.pk & 1023u, sy = (pv.pk >> 10) & 1023u, sz = pv.pk >> 20;
+                T ar = 0, ai = 0;
+                const int nz = DIM == 3 ? W : 1;
+                if (STAGED) {
+                    const int baddr = act ? (sz * a.p1 + sy) * a.p0 + sx + dx : 0;
+#pragma unroll 1
+                    for (int iz = 0; iz < nz; ++iz) {
+                        const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
+                        int addr = baddr + iz * p01;
+                        T zr = 0, zi = 0;
+#pragma unroll
+                        for (int iy = 0; iy < W; ++iy) {
+                            const C t = tile[addr];
+                            zr += wy[iy] * t.x;
+                            zi += wy[iy] * t.y;
+                            addr += a.p0;
                         }
-                        zr += vy * v.x;
-                        zi += vy * v.y;
+                        ar += vz * zr;
+                        ai += vz * zi;
+                    }
+                } else {
+                    const int gx = wrap_any(o0 - P + sx + dx, a.n0);
+#pragma unroll 1
+                    for (int iz = 0; iz < nz; ++iz) {
+                        const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
+                        const int gz = DIM == 3 ? wrap_any(o2 - P + sz + iz, a.n2) : 0;
+                        T zr = 0, zi = 0;
+#pragma unroll
+                        for (int iy = 0; iy < W; ++iy) {
+                            if (act) {
+                                const int gy = wrap_any(o1 - P + sy + iy, a.n1);
+                                const C t = grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx];
+                                zr += wy[iy] * t.x;
+                                zi += wy[iy] * t.y;
+                            }
+                        }
+                        ar += vz * zr;
+                        ai += vz * zi;
                     }
                 }
-                ar += vz * zr;
-                ai += vz * zi;
+                ar = act ? ar * wx : (T)0;
+                ai = act ? ai * wx : (T)0;
+                ar = group_sum<T, W>(ar, dx);
+                ai = group_sum<T, W>(ai, dx);
+                // group totals sit on lanes j*W; hand point i0+j's total to lane i0+j
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    const T tr_ = shfl(ar, j * W), ti_ = shfl(ai, j * W);
+                    if (lane == i0 + j) {
+                        res.x = tr_;
+                        res.y = ti_;
+                    }
+                }
             }
-            ar = group_sum<T, W>(ar * wx, dx);
-            ai = group_sum<T, W>(ai * wx, dx);
-            if (act && dx == 0) {
-                C o;
-                o.x = ar;
-                o.y = ai;
-                cout[a.perm[sub.y + q]] = o;
-            }
+            if (lane < np) cout[myperm] = res;
         }
         if (STAGED) __syncthreads();
     }
@@ -438,7 +490,7 @@ interp_gm_kernel(KArgs<T> a)
     for (int64_t base = gwarp * G; base < total; base += nwarps_total * G) {
         const int64_t item = base + g;
         const bool act = gact && item < total;
-        T wx = 0, wy = 0, wz = 0;
+        T wx = 0, myy = 0, myz = 0;
         int gx = 0, ly0 = 0, lz0 = 0, tr = 0;
         if (act) {
             tr = (int)(item / a.M);
@@ -446,42 +498,40 @@ interp_gm_kernel(KArgs<T> a)
             const AxisPos<T> px = axis_position<T>(period_fraction(a.xyz0[j]), a.n0, W);
             const AxisPos<T> py = axis_position<T>(period_fraction(a.xyz1[j]), a.n1, W);
             wx = es_kernel(((T)dx - px.delta) * a.hw, a.beta);
-            wy = es_kernel(((T)dx - py.delta) * a.hw, a.beta);
+            myy = es_kernel(((T)dx - py.delta) * a.hw, a.beta);
             gx = wrap_any(px.l0 + dx, a.n0);
             ly0 = py.l0;
             if (DIM == 3) {
                 const AxisPos<T> pz = axis_position<T>(period_fraction(a.xyz2[j]), a.n2, W);
-                wz = es_kernel(((T)dx - pz.delta) * a.hw, a.beta);
+                myz = es_kernel(((T)dx - pz.delta) * a.hw, a.beta);
                 lz0 = pz.l0;
             }
         }
+        T wy[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
         const C *grid = a.grid + (int64_t)tr * a.nftot;
         T ar = 0, ai = 0;
         const int nz = DIM == 3 ? W : 1;
 #pragma unroll 1
         for (int iz = 0; iz < nz; ++iz) {
-            T vz = (T)1;
-            int gz = 0;
-            if (DIM == 3) {
-                vz = __shfl_sync(kFullMask, wz, src0 + iz);
-                gz = wrap_any(lz0 + iz, a.n2);
-            }
+            const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
+            const int gz = DIM == 3 ? wrap_any(lz0 + iz, a.n2) : 0;
             T zr = 0, zi = 0;
 #pragma unroll
             for (int iy = 0; iy < W; ++iy) {
-                const T vy = __shfl_sync(kFullMask, wy, src0 + iy);
                 if (act) {
                     const int gy = wrap_any(ly0 + iy, a.n1);
                     const C v = grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx];
-                    zr += vy * v.x;
-                    zi += vy * v.y;
+                    zr += wy[iy] * v.x;
+                    zi += wy[iy] * v.y;
                 }
             }
             ar += vz * zr;
             ai += vz * zi;
         }
-        ar = group_sum<T, W>(ar * wx, dx);
-        ai = group_sum<T, W>(ai * wx, dx);
+        ar = group_sum<T, W>(act ? ar * wx : (T)0, dx);
+        ai = group_sum<T, W>(act ? ai * wx : (T)0, dx);
         if (act && dx == 0) {
             C o;
             o.x = ar;
@@ -519,10 +569,9 @@ KArgs<T> make_args(const Plan &p)
     a.m2 = p.m[2];
     a.nb0 = p.nb[0];
     a.nb1 = p.nb[1];
-    const int P = (p.w + 1) / 2;
-    a.p0 = p.m[0] + 2 * P;
-    a.p1 = p.m[1] + 2 * P;
-    a.p2 = p.dim == 3 ? p.m[2] + 2 * P : 1;
+    a.p0 = padded(p.m[0], p.w);
+    a.p1 = padded(p.m[1], p.w);
+    a.p2 = p.dim == 3 ? padded(p.m[2], p.w) : 1;
     a.beta = (T)p.beta;
     a.hw = (T)(2.0 / p.w);
     return a;
@@ -544,16 +593,15 @@ cudaError_t spread_w(Plan &p, const void *c)
     KArgs<T> a = make_args<T>(p);
     a.cin = reinterpret_cast<const typename cplx<T>::type *>(c);
     const int threads = p.threads;
+    count_launch();
     if (p.method == NUFFT_METHOD_SM) {
         const size_t smem = (size_t)2 * sizeof(T) * a.p0 * a.p1 * a.p2;
         auto k = spread_sm_kernel<T, DIM, W>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int grid = persistent_grid(p, k, threads, smem);
-        count_launch();
         k<<<grid, threads, smem, p.stream>>>(a);
     } else if (p.method == NUFFT_METHOD_GM_SORT) {
         auto k = spread_gmsort_kernel<T, DIM, W>;
-        count_launch();
         k<<<persistent_grid(p, k, threads, 0), threads, 0, p.stream>>>(a);
     } else {
         auto k = spread_gm_kernel<T, DIM, W>;
@@ -562,7 +610,6 @@ cudaError_t spread_w(Plan &p, const void *c)
         const int64_t cap = (int64_t)p.num_sms * 32;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        count_launch();
         k<<<(int)blocks, threads, 0, p.stream>>>(a);
     }
     return cudaGetLastError();
@@ -574,15 +621,14 @@ cudaError_t interp_w(Plan &p, void *c)
     KArgs<T> a = make_args<T>(p);
     a.cout = reinterpret_cast<typename cplx<T>::type *>(c);
     const int threads = p.threads;
+    count_launch();
     if (p.method == NUFFT_METHOD_SM) {
         const size_t smem = sizeof(typename cplx<T>::type) * a.p0 * a.p1 * a.p2;
         auto k = interp_sorted_kernel<T, DIM, W, true>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        count_launch();
         k<<<persistent_grid(p, k, threads, smem), threads, smem, p.stream>>>(a);
     } else if (p.method == NUFFT_METHOD_GM_SORT) {
         auto k = interp_sorted_kernel<T, DIM, W, false>;
-        count_launch();
         k<<<persistent_grid(p, k, threads, 0), threads, 0, p.stream>>>(a);
     } else {
         auto k = interp_gm_kernel<T, DIM, W>;
@@ -591,7 +637,6 @@ cudaError_t interp_w(Plan &p, void *c)
         const int64_t cap = (int64_t)p.num_sms * 32;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        count_launch();
         k<<<(int)blocks, threads, 0, p.stream>>>(a);
     }
     return cudaGetLastError();
