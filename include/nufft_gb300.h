@@ -152,6 +152,36 @@ int nufft_get_sort(nufft_plan plan, int32_t *t, int32_t *bincounts, int32_t *nsu
    all threads).  cuFFT's own kernels are not counted. */
 uint64_t nufft_get_launch_count(void);
 
+/* ---- allocation-free bin-sort ----
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory (code running inside another allocator's callbacks,
+ * real-time or embedded callers with a memory budget fixed at start-up, host
+ * paths that must not take the driver's allocation locks).  It computes the same
+ * stable bin-sort as nufft_setpts -- the permutation t listing the points bin by
+ * bin (increasing original index inside a bin) and the number of points per bin
+ * -- without calling cudaMalloc, cudaFree or any allocating library routine.
+ *
+ *   dim, prec   2 or 3; 0 = float coordinates, 1 = double.
+ *   M           number of points, 0 <= M <= 1048576 (else NUFFT_ERR_SIZE).
+ *   x, y, z     device arrays of M coordinates (z NULL in 2D).
+ *   nf          dim fine-grid sizes n_i (as nufft_get_params reports them).
+ *   bins        dim bin sizes m_i, 1 <= m_i <= n_i; at most 16384 bins in all
+ *               (else NUFFT_ERR_SIZE).
+ *   perm        device int32[M], receives t.
+ *   bincount    device int32[number of bins], receives the counts (x fastest).
+ *   stream      cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Scratch: one fixed device array of about 8.1 MB inside the library, resident
+ * on every device that loads it until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make the
+ * first call on each device before any stream capture.  Every call overwrites
+ * all scratch it uses, but all calls on a device share the one array: calls
+ * whose GPU work could overlap (other streams, other host threads) race and must
+ * be serialised by the caller.  Errors: NUFFT_ERR_ARG, NUFFT_ERR_SIZE,
+ * NUFFT_ERR_CUDA; nothing is written on an argument error. */
+int nufft_binsort_noalloc(int dim, int prec, int64_t M, const void *x, const void *y,
+                          const void *z, const int64_t *nf, const int *bins, int32_t *perm,
+                          int32_t *bincount, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

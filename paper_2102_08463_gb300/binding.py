@@ -32,7 +32,7 @@ EXPORTS = (
     "nufft_default_opts", "nufft_makeplan", "nufft_setpts", "nufft_execute", "nufft_destroy",
     "nufft_strerror", "nufft_spread", "nufft_interp", "nufft_fft", "nufft_deconvolve",
     "nufft_precorrect", "nufft_get_params", "nufft_get_finegrid", "nufft_get_sort",
-    "nufft_spread_add", "nufft_get_launch_count",
+    "nufft_spread_add", "nufft_get_launch_count", "nufft_binsort_noalloc",
 )
 
 
@@ -97,6 +97,8 @@ def load():
         lib.nufft_get_sort.argtypes = [P, P, P, P]
         lib.nufft_spread_add.argtypes = [P, P]
         lib.nufft_get_launch_count.argtypes = []
+        lib.nufft_binsort_noalloc.argtypes = [I, I, I64, P, P, P, ctypes.POINTER(I64),
+                                              ctypes.POINTER(I), P, P, P]
         for name in EXPORTS:
             if name not in ("nufft_default_opts", "nufft_strerror", "nufft_get_launch_count"):
                 getattr(lib, name).restype = I
@@ -167,6 +169,14 @@ def spread(h, c):
 
 def spread_add(h, c):
     _check(load().nufft_spread_add(ctypes.c_void_p(h), c), "nufft_spread_add")
+
+
+def binsort_noalloc(dim, prec, M, x, y, z, nf, bins, perm, bincount, stream=None):
+    """nufft_binsort_noalloc: stable bin-sort into caller buffers, no allocation."""
+    nfa = (ctypes.c_int64 * 3)(*([int(v) for v in nf] + [1] * (3 - len(nf))))
+    ba = (ctypes.c_int * 3)(*([int(v) for v in bins] + [1] * (3 - len(bins))))
+    _check(load().nufft_binsort_noalloc(int(dim), int(prec), int(M), x, y, z, nfa, ba, perm,
+                                        bincount, stream), "nufft_binsort_noalloc")
 
 
 def get_launch_count() -> int:

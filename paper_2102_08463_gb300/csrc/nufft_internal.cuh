@@ -192,6 +192,19 @@ struct Plan {
 // cudaError_t from the last launch.
 cudaError_t launch_setpts(Plan &p, const void *x, const void *y, const void *z);
 cudaError_t launch_scan(Plan &p, const int32_t *in, int32_t *out, int64_t L, int32_t *total);
+
+// Scratch of the bin-sort when the caller supplies it (allocation-free entry point).
+struct BinsortScratch {
+    int32_t *keys;        // [M]
+    int32_t *mat;         // [nblk * nbins]
+    int32_t *binstart;    // [nbins]
+    int32_t *scan_part;   // scan block sums
+    int nblk;             // CTAs of the counting sort
+};
+cudaError_t launch_binsort_into(const BinsortScratch &s, int prec, int dim, int64_t M,
+                                const void *x, const void *y, const void *z, const int64_t *nf,
+                                const int *bins, int32_t *perm, int32_t *bincount,
+                                cudaStream_t st);
 int64_t scan_parts_needed(int64_t L);
 int counting_sort_blocks(const Plan &p, int64_t M);
 int radix_sort_blocks(const Plan &p, int64_t M);

@@ -560,4 +560,75 @@ cudaError_t launch_setpts(Plan &p, const void *x, const void *y, const void *z)
     return setpts_impl<double>(p, (const double *)x, (const double *)y, (const double *)z);
 }
 
+// ---------------------------------------------------------------------------
+// Bin-sort into caller-provided scratch (used by the allocation-free entry
+// point): the counting-sort path above without the packed records.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kCountThreads)
+count_keys_kernel(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z,
+                  int64_t M, int64_t chunk, int3 n, int3 m, int3 nb, int nbins,
+                  int32_t *__restrict__ keys, int32_t *__restrict__ mat)
+{
+    extern __shared__ int hist[];
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(beg + chunk, M);
+    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
+        const int b = bin_of<T, DIM>(x, y, z, j, n, m, nb);
+        keys[j] = b;
+        atomicAdd(&hist[b], 1);
+    }
+    __syncthreads();
+    int32_t *col = mat + (int64_t)blockIdx.x * nbins;
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) col[i] = hist[i];
+}
+
+template <typename T>
+cudaError_t binsort_into_impl(const BinsortScratch &s, int dim, int64_t M, const T *x, const T *y,
+                              const T *z, const int64_t *nf, const int *bins, int32_t *perm,
+                              int32_t *bincount, cudaStream_t st)
+{
+    int3 n = make_int3((int)nf[0], (int)nf[1], dim == 3 ? (int)nf[2] : 1);
+    int3 m = make_int3(bins[0], bins[1], dim == 3 ? bins[2] : 1);
+    int3 nb = make_int3((n.x + m.x - 1) / m.x, (n.y + m.y - 1) / m.y, (n.z + m.z - 1) / m.z);
+    const int nbins = nb.x * nb.y * nb.z;
+    const int64_t chunk = (M + s.nblk - 1) / s.nblk;
+    const size_t smem = (size_t)nbins * sizeof(int32_t);
+    auto kc = dim == 2 ? count_keys_kernel<T, 2> : count_keys_kernel<T, 3>;
+    cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(rank_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launch(3);
+    kc<<<s.nblk, kCountThreads, smem, st>>>(x, y, z, M, chunk, n, m, nb, nbins, s.keys, s.mat);
+    column_scan_kernel<<<(nbins + 255) / 256, 256, 0, st>>>(s.mat, nbins, s.nblk, bincount);
+    Plan scan_plan;                 // only scan_part and stream are used by launch_scan
+    scan_plan.stream = st;
+    scan_plan.scan_part = s.scan_part;
+    e = launch_scan(scan_plan, bincount, s.binstart, nbins, nullptr);
+    if (e != cudaSuccess) return e;
+    rank_scatter_kernel<<<s.nblk, kCountThreads, smem, st>>>(M, chunk, nbins, s.keys, s.mat,
+                                                             s.binstart, perm);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_binsort_into(const BinsortScratch &s, int prec, int dim, int64_t M,
+                                const void *x, const void *y, const void *z, const int64_t *nf,
+                                const int *bins, int32_t *perm, int32_t *bincount,
+                                cudaStream_t st)
+{
+    if (prec == 0)
+        return binsort_into_impl<float>(s, dim, M, (const float *)x, (const float *)y,
+                                        (const float *)z, nf, bins, perm, bincount, st);
+    return binsort_into_impl<double>(s, dim, M, (const double *)x, (const double *)y,
+                                     (const double *)z, nf, bins, perm, bincount, st);
+}
+
 }  // namespace nufft
