@@ -87,8 +87,9 @@ void nufft_default_opts(nufft_opts *opts);
  *   eps     requested relative tolerance; kernel width w = ceil(log10(1/eps)) + 1
  *           (clamped to [2, 16]), beta = 2.30 w, fine grid n_i = smallest
  *           2^a 3^b 5^c >= max(sigma N_i, 2w).
- *   prec    0 = single, 1 = double, -1 = by tolerance (single if eps >= 1e-6).
- *           Single precision requires eps >= 1e-6 (NUFFT_ERR_EPS otherwise).
+ *   prec    0 = single, 1 = double, -1 = by tolerance (single if eps >= 1e-6;
+ *           with upsampfac 1.25, single if eps >= 1e-4).  Single precision
+ *           requires those tolerances (NUFFT_ERR_EPS otherwise).
  *   opts    NULL for defaults.
  *   out     receives the plan handle (NULL on failure).
  * Allocates the fine grid (ntransf * n1*n2(*n3) complex), the correction factors

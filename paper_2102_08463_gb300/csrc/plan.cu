@@ -198,8 +198,12 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     if (o.msub < 0 || o.threads < 0 || o.ctas_per_sm < 0) return NUFFT_ERR_ARG;
     if (o.threads != 0 && (o.threads % 32 != 0 || o.threads > 256)) return NUFFT_ERR_ARG;
 
-    if (prec == -1) prec = eps >= 1e-6 ? 0 : 1;
-    if (prec == 0 && eps < 1e-6) return NUFFT_ERR_EPS;
+    // Single precision reaches 1e-6 at sigma = 2; at sigma = 1.25 the correction
+    // factors span ~100x more, which amplifies single-precision rounding of the
+    // fine grid to ~1e-4, so single precision there needs eps >= 1e-4.
+    const double fp32_floor = sigma == 2.0 ? 1e-6 : 1e-4;
+    if (prec == -1) prec = eps >= fp32_floor ? 0 : 1;
+    if (prec == 0 && eps < fp32_floor) return NUFFT_ERR_EPS;
     int w = kernel_width(eps, sigma);
     if (w > kMaxW) return NUFFT_ERR_EPS;
 

@@ -306,3 +306,61 @@ def test_errors(nb):
         nb.execute(h, None, nb._dptr(torch.empty(64, dtype=torch.complex64, device="cuda")))
     assert e.value.code == nb.NUFFT_ERR_NOPTS
     nb.destroy(h)
+
+
+def _amplification(N, eps, sigma):
+    """RMS over the retained modes of |p_k| / |p_0| (product over axes): the factor by
+    which the correction step (Sec. 3.1 step 3) magnifies rounding noise of the fine
+    grid's transform.  About 2-5 at sigma = 2; 10^2-10^5 at sigma = 1.25."""
+    P = oracle.Params(N, eps, sigma)
+    amp = 1.0
+    for Ni, ni in zip(P.N, P.n):
+        p1 = np.abs(oracle.correction_1d(Ni, ni, P.w, P.beta))
+        amp *= np.sqrt(np.mean(p1 ** 2)) / p1[Ni // 2]
+    return amp
+
+
+@pytest.mark.parametrize("type_", [1, 2])
+@pytest.mark.parametrize("dim,eps,prec", [(2, 1e-4, 0), (3, 1e-4, 0), (2, 1e-9, 1), (3, 1e-8, 1)])
+def test_sigma125(nb, type_, dim, eps, prec):
+    N = (48, 40) if dim == 2 else (20, 18, 16)
+    M = 5000
+    dt = np.float32 if prec == 0 else np.float64
+    ct = np.complex64 if prec == 0 else np.complex128
+    pts = wl.points("rand", dim, M, 77 + dim, dt)
+    p64 = [q.astype(np.float64) for q in pts]
+    p = _plan(nb, type_, N, eps, prec, upsampfac=1.25)
+    assert tuple(p.params["nf"][:dim]) == oracle.Params(N, eps, 1.25).n
+    p.setpts(*_pts_dev(pts, prec))
+    w = p.params["w"]
+    if type_ == 1:
+        c = wl.strengths(M, 78, ct)
+        got = _host(p.execute(c=_dev(c)))
+        same_w = oracle.nufft_type1(p64, c.astype(np.complex128), N, w=w, sigma=1.25)
+        exact = oracle.direct_type1(p64, c.astype(np.complex128), N)
+    else:
+        f = wl.modes(N, 79, ct)
+        got = _host(p.execute(f=_dev(f)))
+        same_w = oracle.nufft_type2(p64, f.astype(np.complex128), w=w, sigma=1.25)
+        exact = oracle.direct_type2(p64, f.astype(np.complex128))
+    # rounding allowance: unit roundoff times the correction-factor amplification
+    u = 6e-8 if prec == 0 else 1.1e-16
+    tol = max(_tol(prec), 4 * u * _amplification(N, eps, 1.25))
+    assert oracle.rel_l2(got, same_w) < tol
+    assert oracle.rel_l2(got, exact) <= max(2 * eps, oracle.rel_l2(same_w, exact) + tol)
+    p.close()
+
+
+def test_sigma125_single_precision_floor(nb):
+    with pytest.raises(nb.NufftError) as e:
+        nb.makeplan(1, 2, (32, 32), eps=1e-6, prec=0, opts=_opts125(nb))
+    assert e.value.code == nb.NUFFT_ERR_EPS
+    h = nb.makeplan(1, 2, (32, 32), eps=1e-6, prec=-1, opts=_opts125(nb))
+    assert nb.get_params(h)["prec"] == 1
+    nb.destroy(h)
+
+
+def _opts125(nb):
+    o = nb.default_opts()
+    o.upsampfac = 1.25
+    return o

@@ -299,3 +299,21 @@ def test_subproblems_cover_each_bin():
     for b, cnt in enumerate(counts):
         assert rows[rows[:, 0] == b, 2].sum() == cnt
     assert np.array_equal(rows[:, 1], np.concatenate([[0], np.cumsum(rows[:, 2])[:-1]]))
+
+
+# ---------------------------------------------------------------------------
+# sigma = 1.25 (not in the paper; the width / shape reading is checked here
+# against the exact sums, which are pinned above)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-6, 1e-8])
+def test_sigma125_width_rule_meets_eps(eps):
+    N, M = (40, 36), 3000
+    pts = _pts(2, M, 41)
+    c = wl.strengths(M, 42, np.complex128)
+    exact = oracle.direct_type1(pts, c, N)
+    w = oracle.kernel_width(eps, 1.25)
+    e_w = oracle.rel_l2(oracle.nufft_type1(pts, c, N, w=w, sigma=1.25), exact)
+    e_w1 = oracle.rel_l2(oracle.nufft_type1(pts, c, N, w=w - 1, sigma=1.25), exact)
+    assert e_w <= eps            # the calibrated width reaches the tolerance
+    assert e_w1 > e_w            # one cell narrower is measurably worse
+    assert oracle.Params(N, eps, 1.25).n == (50, 45)   # 2^a 3^b 5^c >= 1.25 N
