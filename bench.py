@@ -63,7 +63,11 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic per launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel and workload, with the hash of the
 # kernel sources at capture time; a stale hash reports null.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/spread_interp_2d-1024-rand-eps1e-5.md
+    "spread:2d-1024-rand-eps1e-5:a0fe1669739a7c2b": 395570688,
+    "interp:2d-1024-rand-eps1e-5:a0fe1669739a7c2b": 312735488,
+}
 
 
 def _src_hash():
