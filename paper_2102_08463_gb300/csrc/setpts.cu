@@ -11,7 +11,7 @@
 //     bin totals gives every CTA the first output slot of each of its bins; the
 //     CTA then walks its chunk in order, ranks equal bins inside each tile with
 //     __match_any_sync (lanes) and warp order (one barrier per warp), and writes
-//     t and the packed record of each point straight to its sorted slot.
+//     each point's index into its sorted slot of t.
 //   LSD radix sort (many bins): 8-bit digits, per-CTA digit histograms, a scan
 //     of the digit x CTA matrix, ranked scatter.
 // The packed records are written in the original point order (coalesced); the
@@ -186,7 +186,7 @@ __device__ __forceinline__ typename rec4<T>::type make_record_v(T xv, T yv, T zv
 // (mat[cta * nbins + bin], coalesced).  Four points per thread per round keep
 // several loads in flight.
 // ---------------------------------------------------------------------------
-constexpr int kCountThreads = 1024;
+constexpr int kCountThreads = 512;
 constexpr int kCountUnroll = 4;
 
 template <typename T, int DIM>
@@ -234,30 +234,37 @@ count_kernel(const T *__restrict__ x, const T *__restrict__ y, const T *__restri
 
 // Counting sort, pass 2: per bin, exclusive prefix over the CTAs (in place) and
 // the bin total.
-__global__ void column_scan_kernel(int32_t *__restrict__ mat, int nbins, int nblk,
-                                   int32_t *__restrict__ bincount)
+constexpr int kColWarps = 8;
+
+// 32 bins per CTA (lane = bin, coalesced rows); each warp owns a slice of the
+// CTA rows: slice sums, exclusive prefix over slices, then a rescan of the slice.
+__global__ void __launch_bounds__(kColWarps * 32)
+column_scan_kernel(int32_t *__restrict__ mat, int nbins, int nblk, int32_t *__restrict__ bincount)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbins) return;
+    __shared__ int part[kColWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * 32 + lane;
+    const bool ok = b < nbins;
+    const int r0 = (int)((int64_t)nblk * warp / kColWarps);
+    const int r1 = (int)((int64_t)nblk * (warp + 1) / kColWarps);
     int s = 0;
-    int cta = 0;
-    for (; cta + 4 <= nblk; cta += 4) {
-        const int v0 = mat[(int64_t)cta * nbins + b];
-        const int v1 = mat[(int64_t)(cta + 1) * nbins + b];
-        const int v2 = mat[(int64_t)(cta + 2) * nbins + b];
-        const int v3 = mat[(int64_t)(cta + 3) * nbins + b];
-        mat[(int64_t)cta * nbins + b] = s;
-        mat[(int64_t)(cta + 1) * nbins + b] = s + v0;
-        mat[(int64_t)(cta + 2) * nbins + b] = s + v0 + v1;
-        mat[(int64_t)(cta + 3) * nbins + b] = s + v0 + v1 + v2;
-        s += v0 + v1 + v2 + v3;
+    if (ok) {
+#pragma unroll 4
+        for (int r = r0; r < r1; ++r) s += mat[(int64_t)r * nbins + b];
     }
-    for (; cta < nblk; ++cta) {
-        const int v = mat[(int64_t)cta * nbins + b];
-        mat[(int64_t)cta * nbins + b] = s;
-        s += v;
+    part[warp][lane] = s;
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += part[w][lane];
+    if (ok) {
+        if (warp == kColWarps - 1) bincount[b] = off + s;
+        for (int r = r0; r < r1; ++r) {
+            const int64_t i = (int64_t)r * nbins + b;
+            const int v = mat[i];
+            mat[i] = off;
+            off += v;
+        }
     }
-    bincount[b] = s;
 }
 
 // Counting sort, pass 3: stable ranked scatter of t.  The next tile's keys are
@@ -448,7 +455,7 @@ int counting_sort_blocks(const Plan &p, int64_t M)
     const size_t smem = (size_t)p.nbins * sizeof(int32_t);
     if (smem > (size_t)p.smem_optin) return 0;
     int per_sm = (int)((size_t)p.smem_per_sm / (smem + 1024));
-    if (per_sm > 2) per_sm = 2;            // 2 x 1024 threads fill an SM
+    if (per_sm > 4) per_sm = 4;            // 4 x 512 threads fill an SM
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)p.num_sms * per_sm;
     const int64_t by_size = (M + 8191) / 8192;
@@ -492,7 +499,7 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
         count_launch(3);
         kc<<<cblk, kCountThreads, smem, st>>>(x, y, z, M, chunk, n, m, nb, nbins, p.w, p.keys,
                                               p.mat, recs);
-        column_scan_kernel<<<(nbins + 255) / 256, 256, 0, st>>>(p.mat, nbins, cblk, p.bincount);
+        column_scan_kernel<<<(nbins + 31) / 32, kColWarps * 32, 0, st>>>(p.mat, nbins, cblk, p.bincount);
         e = launch_scan(p, p.bincount, p.binstart, nbins, nullptr);
         if (e != cudaSuccess) return e;
         ks<<<cblk, kCountThreads, smem, st>>>(M, chunk, nbins, p.keys, p.mat, p.binstart, p.vals);
@@ -606,7 +613,7 @@ cudaError_t binsort_into_impl(const BinsortScratch &s, int dim, int64_t M, const
     if (e != cudaSuccess) return e;
     count_launch(3);
     kc<<<s.nblk, kCountThreads, smem, st>>>(x, y, z, M, chunk, n, m, nb, nbins, s.keys, s.mat);
-    column_scan_kernel<<<(nbins + 255) / 256, 256, 0, st>>>(s.mat, nbins, s.nblk, bincount);
+    column_scan_kernel<<<(nbins + 31) / 32, kColWarps * 32, 0, st>>>(s.mat, nbins, s.nblk, bincount);
     Plan scan_plan;                 // only scan_part and stream are used by launch_scan
     scan_plan.stream = st;
     scan_plan.scan_part = s.scan_part;
