@@ -153,6 +153,30 @@ int nufft_get_sort(nufft_plan plan, int32_t *t, int32_t *bincounts, int32_t *nsu
    all threads).  cuFFT's own kernels are not counted. */
 uint64_t nufft_get_launch_count(void);
 
+/* ---- batched execution of many plans ----
+ * Not in the paper (its interface runs one plan at a time); for workloads of
+ * many independent transforms of uneven N and M.  Plans that share type,
+ * dimension, precision, kernel width and method (SM or GM-sort) are grouped, and
+ * each group's spreading / interpolation runs as one persistent launch over the
+ * subproblems of all its plans; clears, corrections and cuFFT stay per plan.
+ *
+ * nufft_batch_create: plans[0..nplans) must be distinct and set up (setpts)
+ *   before each execute; while the batch exists they run on `stream` (their cuFFT
+ *   plans are re-bound to it) and must not be used on their own.  Destroying the
+ *   batch hands them back their own streams.
+ * nufft_batch_execute: c[k], f[k] are the plan-k arrays of nufft_execute.
+ * nufft_batch_capture: records the execute of these c / f arrays into a CUDA
+ *   graph (stream must not be NULL); nufft_batch_launch replays it.  Re-running
+ *   setpts on a member with the same M keeps the graph valid; a larger M or a new
+ *   subproblem capacity reallocates and needs a new capture.
+ * Errors as nufft_execute; NUFFT_ERR_NOPTS from launch when nothing was captured. */
+typedef struct nufft_batch_s *nufft_batch;
+int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_batch *out);
+int nufft_batch_execute(nufft_batch batch, void *const *c, void *const *f);
+int nufft_batch_capture(nufft_batch batch, void *const *c, void *const *f);
+int nufft_batch_launch(nufft_batch batch);
+int nufft_batch_destroy(nufft_batch batch);
+
 /* ---- allocation-free bin-sort ----
  * The paper has no counterpart: this entry point exists for callers that cannot
  * allocate device memory (code running inside another allocator's callbacks,

@@ -33,6 +33,8 @@ EXPORTS = (
     "nufft_strerror", "nufft_spread", "nufft_interp", "nufft_fft", "nufft_deconvolve",
     "nufft_precorrect", "nufft_get_params", "nufft_get_finegrid", "nufft_get_sort",
     "nufft_spread_add", "nufft_get_launch_count", "nufft_binsort_noalloc",
+    "nufft_batch_create", "nufft_batch_execute", "nufft_batch_capture", "nufft_batch_launch",
+    "nufft_batch_destroy",
 )
 
 
@@ -97,6 +99,11 @@ def load():
         lib.nufft_get_sort.argtypes = [P, P, P, P]
         lib.nufft_spread_add.argtypes = [P, P]
         lib.nufft_get_launch_count.argtypes = []
+        lib.nufft_batch_create.argtypes = [ctypes.POINTER(P), I, P, ctypes.POINTER(P)]
+        lib.nufft_batch_execute.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P)]
+        lib.nufft_batch_capture.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P)]
+        lib.nufft_batch_launch.argtypes = [P]
+        lib.nufft_batch_destroy.argtypes = [P]
         lib.nufft_binsort_noalloc.argtypes = [I, I, I64, P, P, P, ctypes.POINTER(I64),
                                               ctypes.POINTER(I), P, P, P]
         for name in EXPORTS:
@@ -177,6 +184,57 @@ def binsort_noalloc(dim, prec, M, x, y, z, nf, bins, perm, bincount, stream=None
     ba = (ctypes.c_int * 3)(*([int(v) for v in bins] + [1] * (3 - len(bins))))
     _check(load().nufft_binsort_noalloc(int(dim), int(prec), int(M), x, y, z, nfa, ba, perm,
                                         bincount, stream), "nufft_binsort_noalloc")
+
+
+class Batch:
+    """Batched execution of several Plan objects (nufft_batch_*).
+
+    Batch(plans, stream=None): plans must have their points set.  execute(cs, fs)
+    runs all transforms (cs[k], fs[k] as Plan.execute would take / fill);
+    capture(cs, fs) records a CUDA graph that launch() replays.
+    """
+
+    def __init__(self, plans, stream=None):
+        import torch
+        self.plans = list(plans)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(load().nufft_batch_create(arr, len(self.plans), ctypes.c_void_p(stream.cuda_stream),
+                                         ctypes.byref(h)), "nufft_batch_create")
+        self.handle = h.value
+
+    def _ptrs(self, cs, fs):
+        n = len(self.plans)
+        c = (ctypes.c_void_p * n)(*[ctypes.c_void_p(x.data_ptr()) if x is not None else None
+                                    for x in cs])
+        f = (ctypes.c_void_p * n)(*[ctypes.c_void_p(x.data_ptr()) for x in fs])
+        self._keep = (cs, fs)
+        return c, f
+
+    def execute(self, cs, fs):
+        c, f = self._ptrs(cs, fs)
+        _check(load().nufft_batch_execute(ctypes.c_void_p(self.handle), c, f), "nufft_batch_execute")
+
+    def capture(self, cs, fs):
+        c, f = self._ptrs(cs, fs)
+        _check(load().nufft_batch_capture(ctypes.c_void_p(self.handle), c, f), "nufft_batch_capture")
+
+    def launch(self):
+        _check(load().nufft_batch_launch(ctypes.c_void_p(self.handle)), "nufft_batch_launch")
+
+    def close(self):
+        if self.handle:
+            load().nufft_batch_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def get_launch_count() -> int:

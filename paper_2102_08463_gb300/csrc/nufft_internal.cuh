@@ -30,7 +30,7 @@ template <> struct cplx<double> { using type = double2; };
 // stored in the last slot.
 template <typename T> struct rec4;
 template <> struct rec4<float> { using type = float4; };
-template <> struct rec4<double> { using type = double4; };
+template <> struct rec4<double> { using type = double4_32a; };
 
 struct Plan;
 
@@ -216,9 +216,34 @@ cudaError_t interp_f32_2d(Plan &p, void *c);
 cudaError_t interp_f32_3d(Plan &p, void *c);
 cudaError_t interp_f64_2d(Plan &p, void *c);
 cudaError_t interp_f64_3d(Plan &p, void *c);
+
+// One grouped launch over several plans of equal type, dimension, precision,
+// width and method (batched execution): per-plan kernel arguments in device
+// memory, workoff[p] = first global work item of plan p (workoff[nplans] = total).
+struct MultiLaunch {
+    const void *args;          // device array of KArgs<T>, one per plan
+    const int64_t *workoff;    // device [nplans + 1]
+    int nplans;
+    int w, method, threads, num_sms;
+    size_t smem;               // shared memory per CTA (max over the plans)
+    cudaStream_t stream;
+};
+cudaError_t spread_multi_f32_2d(const MultiLaunch &ml);
+cudaError_t spread_multi_f32_3d(const MultiLaunch &ml);
+cudaError_t spread_multi_f64_2d(const MultiLaunch &ml);
+cudaError_t spread_multi_f64_3d(const MultiLaunch &ml);
+cudaError_t interp_multi_f32_2d(const MultiLaunch &ml);
+cudaError_t interp_multi_f32_3d(const MultiLaunch &ml);
+cudaError_t interp_multi_f64_2d(const MultiLaunch &ml);
+cudaError_t interp_multi_f64_3d(const MultiLaunch &ml);
 cudaError_t launch_deconvolve(Plan &p, void *f);
 cudaError_t launch_precorrect(Plan &p, const void *f);
 cudaError_t launch_zero(Plan &p, void *ptr, size_t bytes);
 cudaError_t launch_correction(Plan &p, const double *gl_t, const double *gl_w, int nq);
 
 }  // namespace nufft
+
+// The opaque handle of the C ABI.
+struct nufft_plan_s {
+    nufft::Plan p;
+};

@@ -14,10 +14,6 @@ using namespace nufft;
 
 std::atomic<unsigned long long> nufft::g_launch_count{0};
 
-struct nufft_plan_s {
-    Plan p;
-};
-
 namespace {
 
 int next235(int64_t n)
@@ -357,7 +353,7 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
     if (M > p.Mcap || maxsub > p.maxsub) {
         free_points(p);
         const int64_t cap = M > 0 ? M : 1;
-        const size_t rsz = p.prec == 0 ? sizeof(float4) : sizeof(double4);
+        const size_t rsz = p.prec == 0 ? sizeof(float4) : sizeof(double4_32a);
         int rc = dev_alloc(&p.keys, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.keys_alt, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.vals, sizeof(int32_t) * cap);

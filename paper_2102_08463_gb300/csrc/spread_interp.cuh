@@ -107,19 +107,18 @@ __device__ __forceinline__ PointView<T> take_point(const typename rec4<T>::type 
 }
 
 // ---------------------------------------------------------------------------
-// SM spreading.
+// SM spreading.  One work item = one (subproblem, transform) pair, run by the
+// whole CTA; the single-plan kernel and the multi-plan (batched) kernel below
+// both stride over work items.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int W>
-__global__ void __launch_bounds__(256)
-spread_sm_kernel(KArgs<T> a)
+__device__ __forceinline__ void spread_sm_item(const KArgs<T> &a, int sp, int tr, T *sre)
 {
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int G = 32 / W;
     const int ptot = a.p0 * a.p1 * (DIM == 3 ? a.p2 : 1);
     const int p01 = a.p0 * a.p1;
-    T *sre = reinterpret_cast<T *>(smem_raw);
     T *sim = sre + ptot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -127,11 +126,7 @@ spread_sm_kernel(KArgs<T> a)
     const bool gact = g < G;
     const int src0 = (gact ? g : G - 1) * W;
     const int P = pad_lo(W);
-    const int nsp = *a.nsub;
-    const int64_t nwork = (int64_t)nsp * a.ntransf;
-    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-        const int sp = (int)(wi % nsp);
-        const int tr = (int)(wi / nsp);
+    {
         const int4 sub = a.subprob[sp];
         for (int i = threadIdx.x; i < 2 * ptot; i += blockDim.x) sre[i] = (T)0;
         __syncthreads();
@@ -198,12 +193,52 @@ spread_sm_kernel(KArgs<T> a)
     }
 }
 
+template <typename T, int DIM, int W>
+__global__ void __launch_bounds__(256)
+spread_sm_kernel(KArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sre = reinterpret_cast<T *>(smem_raw);
+    const int nsp = *a.nsub;
+    const int64_t nwork = (int64_t)nsp * a.ntransf;
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x)
+        spread_sm_item<T, DIM, W>(a, (int)(wi % nsp), (int)(wi / nsp), sre);
+}
+
+// Plan of global work item wi in a batch: workoff[p] <= wi < workoff[p + 1].
+__device__ __forceinline__ int batch_plan_of(const int64_t *workoff, int nplans, int64_t wi)
+{
+    int lo = 0, hi = nplans - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (workoff[mid] <= wi) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int DIM, int W>
+__global__ void __launch_bounds__(256)
+spread_sm_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
+                       int nplans)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sre = reinterpret_cast<T *>(smem_raw);
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        const KArgs<T> a = args[pl];
+        const int64_t local = wi - workoff[pl];
+        const int nsp = *a.nsub;
+        spread_sm_item<T, DIM, W>(a, (int)(local % nsp), (int)(local / nsp), sre);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // GM-sort spreading: bin-ordered points, global atomics.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int W>
-__global__ void __launch_bounds__(256)
-spread_gmsort_kernel(KArgs<T> a)
+__device__ __forceinline__ void spread_gmsort_item(const KArgs<T> &a, int sp, int tr)
 {
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
@@ -214,11 +249,7 @@ spread_gmsort_kernel(KArgs<T> a)
     const bool gact = g < G;
     const int src0 = (gact ? g : G - 1) * W;
     const int P = pad_lo(W);
-    const int nsp = *a.nsub;
-    const int64_t nwork = (int64_t)nsp * a.ntransf;
-    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-        const int sp = (int)(wi % nsp);
-        const int tr = (int)(wi / nsp);
+    {
         const int4 sub = a.subprob[sp];
         int o0, o1, o2;
         bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
@@ -266,6 +297,31 @@ spread_gmsort_kernel(KArgs<T> a)
                 }
             }
         }
+    }
+}
+
+template <typename T, int DIM, int W>
+__global__ void __launch_bounds__(256)
+spread_gmsort_kernel(KArgs<T> a)
+{
+    const int nsp = *a.nsub;
+    const int64_t nwork = (int64_t)nsp * a.ntransf;
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x)
+        spread_gmsort_item<T, DIM, W>(a, (int)(wi % nsp), (int)(wi / nsp));
+}
+
+template <typename T, int DIM, int W>
+__global__ void __launch_bounds__(256)
+spread_gmsort_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
+                           int nplans)
+{
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        const KArgs<T> a = args[pl];
+        const int64_t local = wi - workoff[pl];
+        const int nsp = *a.nsub;
+        spread_gmsort_item<T, DIM, W>(a, (int)(local % nsp), (int)(local / nsp));
     }
 }
 
@@ -351,13 +407,11 @@ __device__ __forceinline__ T group_sum(T v, int dx)
 // loaded the point, so the batch writes its 32 results together.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int W, bool STAGED>
-__global__ void __launch_bounds__(256)
-interp_sorted_kernel(KArgs<T> a)
+__device__ __forceinline__ void interp_sorted_item(const KArgs<T> &a, int sp, int tr,
+                                                   typename cplx<T>::type *tile)
 {
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tile = reinterpret_cast<C *>(smem_raw);
     constexpr int G = 32 / W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -366,11 +420,7 @@ interp_sorted_kernel(KArgs<T> a)
     const int src0 = (gact ? g : G - 1) * W;
     const int P = pad_lo(W);
     const int p01 = a.p0 * a.p1;
-    const int nsp = *a.nsub;
-    const int64_t nwork = (int64_t)nsp * a.ntransf;
-    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-        const int sp = (int)(wi % nsp);
-        const int tr = (int)(wi / nsp);
+    {
         const int4 sub = a.subprob[sp];
         int o0, o1, o2;
         bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
@@ -468,6 +518,35 @@ interp_sorted_kernel(KArgs<T> a)
             if (lane < np) cout[myperm] = res;
         }
         if (STAGED) __syncthreads();
+    }
+}
+
+template <typename T, int DIM, int W, bool STAGED>
+__global__ void __launch_bounds__(256)
+interp_sorted_kernel(KArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto *tile = reinterpret_cast<typename cplx<T>::type *>(smem_raw);
+    const int nsp = *a.nsub;
+    const int64_t nwork = (int64_t)nsp * a.ntransf;
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x)
+        interp_sorted_item<T, DIM, W, STAGED>(a, (int)(wi % nsp), (int)(wi / nsp), tile);
+}
+
+template <typename T, int DIM, int W, bool STAGED>
+__global__ void __launch_bounds__(256)
+interp_sorted_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
+                           int nplans)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto *tile = reinterpret_cast<typename cplx<T>::type *>(smem_raw);
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        const KArgs<T> a = args[pl];
+        const int64_t local = wi - workoff[pl];
+        const int nsp = *a.nsub;
+        interp_sorted_item<T, DIM, W, STAGED>(a, (int)(local % nsp), (int)(local / nsp), tile);
     }
 }
 
@@ -642,6 +721,70 @@ cudaError_t interp_w(Plan &p, void *c)
     return cudaGetLastError();
 }
 
+template <typename T, int DIM, int W>
+cudaError_t spread_multi_w(const MultiLaunch &ml)
+{
+    const auto *args = reinterpret_cast<const KArgs<T> *>(ml.args);
+    count_launch();
+    if (ml.method == NUFFT_METHOD_SM) {
+        auto k = spread_sm_multi_kernel<T, DIM, W>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ml.smem);
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, ml.threads, ml.smem);
+        k<<<ml.num_sms * (per < 1 ? 1 : per), ml.threads, ml.smem, ml.stream>>>(args, ml.workoff,
+                                                                                ml.nplans);
+    } else {
+        auto k = spread_gmsort_multi_kernel<T, DIM, W>;
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, ml.threads, 0);
+        k<<<ml.num_sms * (per < 1 ? 1 : per), ml.threads, 0, ml.stream>>>(args, ml.workoff,
+                                                                          ml.nplans);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int DIM, int W>
+cudaError_t interp_multi_w(const MultiLaunch &ml)
+{
+    const auto *args = reinterpret_cast<const KArgs<T> *>(ml.args);
+    count_launch();
+    if (ml.method == NUFFT_METHOD_SM) {
+        auto k = interp_sorted_multi_kernel<T, DIM, W, true>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ml.smem);
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, ml.threads, ml.smem);
+        k<<<ml.num_sms * (per < 1 ? 1 : per), ml.threads, ml.smem, ml.stream>>>(args, ml.workoff,
+                                                                                ml.nplans);
+    } else {
+        auto k = interp_sorted_multi_kernel<T, DIM, W, false>;
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, ml.threads, 0);
+        k<<<ml.num_sms * (per < 1 ? 1 : per), ml.threads, 0, ml.stream>>>(args, ml.workoff,
+                                                                          ml.nplans);
+    }
+    return cudaGetLastError();
+}
+
+#define NUFFT_W_SWITCH_ON(WV, FN, T, DIM, ...)                                \
+    switch (WV) {                                                             \
+    case 2: return FN<T, DIM, 2>(__VA_ARGS__);                                \
+    case 3: return FN<T, DIM, 3>(__VA_ARGS__);                                \
+    case 4: return FN<T, DIM, 4>(__VA_ARGS__);                                \
+    case 5: return FN<T, DIM, 5>(__VA_ARGS__);                                \
+    case 6: return FN<T, DIM, 6>(__VA_ARGS__);                                \
+    case 7: return FN<T, DIM, 7>(__VA_ARGS__);                                \
+    case 8: return FN<T, DIM, 8>(__VA_ARGS__);                                \
+    case 9: return FN<T, DIM, 9>(__VA_ARGS__);                                \
+    case 10: return FN<T, DIM, 10>(__VA_ARGS__);                              \
+    case 11: return FN<T, DIM, 11>(__VA_ARGS__);                              \
+    case 12: return FN<T, DIM, 12>(__VA_ARGS__);                              \
+    case 13: return FN<T, DIM, 13>(__VA_ARGS__);                              \
+    case 14: return FN<T, DIM, 14>(__VA_ARGS__);                              \
+    case 15: return FN<T, DIM, 15>(__VA_ARGS__);                              \
+    case 16: return FN<T, DIM, 16>(__VA_ARGS__);                              \
+    default: return cudaErrorInvalidValue;                                    \
+    }
+
 #define NUFFT_W_SWITCH(FN, T, DIM, ...)                                       \
     switch (p.w) {                                                            \
     case 2: return FN<T, DIM, 2>(__VA_ARGS__);                                \
@@ -662,7 +805,8 @@ cudaError_t interp_w(Plan &p, void *c)
     default: return cudaErrorInvalidValue;                                    \
     }
 
-// One translation unit per (T, DIM) defines spread_<tag> and interp_<tag>.
+// One translation unit per (T, DIM) defines spread_<tag>, interp_<tag> and
+// their multi-plan (batched) forms.
 #define NUFFT_INSTANTIATE_SI(T, DIM, TAG)                                     \
     cudaError_t spread_##TAG(Plan &p, const void *c)                          \
     {                                                                         \
@@ -671,6 +815,14 @@ cudaError_t interp_w(Plan &p, void *c)
     cudaError_t interp_##TAG(Plan &p, void *c)                                \
     {                                                                         \
         NUFFT_W_SWITCH(interp_w, T, DIM, p, c)                                \
+    }                                                                         \
+    cudaError_t spread_multi_##TAG(const MultiLaunch &ml)                     \
+    {                                                                         \
+        NUFFT_W_SWITCH_ON(ml.w, spread_multi_w, T, DIM, ml)                   \
+    }                                                                         \
+    cudaError_t interp_multi_##TAG(const MultiLaunch &ml)                     \
+    {                                                                         \
+        NUFFT_W_SWITCH_ON(ml.w, interp_multi_w, T, DIM, ml)                   \
     }
 
 }  // namespace nufft
