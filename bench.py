@@ -492,12 +492,148 @@ def run_reference(args, W, rank):
     }
 
 
+# ---------------------------------------------------------------------------
+# Many-plan workload: 256 independent plans of uneven N and M plus one
+# ntransf = 32 plan, one-by-one with the heuristic tiles versus autotuned tiles
+# in one captured batched launch.
+# ---------------------------------------------------------------------------
+def batch_specs(seed=SEED + 40):
+    """256 plans: half 2D / half 3D, half type 1 / half type 2; square / cube N
+    log-uniform in [32, 512] (2D) or [16, 128] (3D); M log-uniform in [1e4, 2e6];
+    plus one 2D N = 512^2, M = 1e6, ntransf = 32 plan.  eps = 1e-5, single precision."""
+    u = wl.uniform01(seed, 4 * 256, stream=50).reshape(256, 4)
+    specs = []
+    for i in range(256):
+        dim = 2 if i % 2 == 0 else 3
+        tp = 1 if (i // 2) % 2 == 0 else 2
+        lo, hi = (32, 512) if dim == 2 else (16, 128)
+        n1 = int(round(math.exp(math.log(lo) + u[i, 0] * (math.log(hi) - math.log(lo)))))
+        M = int(round(math.exp(math.log(1e4) + u[i, 1] * (math.log(2e6) - math.log(1e4)))))
+        specs.append(dict(type=tp, N=(n1,) * dim, M=M, ntransf=1))
+    specs.append(dict(type=1, N=(512, 512), M=1000000, ntransf=32))
+    return specs
+
+
+def run_batch_bench(args):
+    import torch
+    from paper_2102_08463_gb300 import binding
+
+    stream = torch.cuda.Stream()
+    specs = batch_specs()
+    eps = 1e-5
+    torch.cuda.set_device(0)
+    with torch.cuda.stream(stream):
+        data = []
+        for i, sp in enumerate(specs):
+            dim = len(sp["N"])
+            pts = [torch.from_numpy(a).cuda() for a in wl.points("rand", dim, sp["M"], SEED + 1000 + i,
+                                                                 np.float32)]
+            if sp["type"] == 1:
+                c = torch.from_numpy(wl.strengths(sp["M"], SEED + 3000 + i, np.complex64,
+                                                  ntransf=sp["ntransf"])).cuda()
+                shp = tuple(reversed(sp["N"]))
+                f = torch.zeros(((sp["ntransf"],) + shp) if sp["ntransf"] > 1 else shp,
+                                dtype=torch.complex64, device="cuda")
+            else:
+                f = torch.from_numpy(wl.modes(sp["N"], SEED + 5000 + i, np.complex64)).cuda()
+                c = torch.zeros(sp["M"], dtype=torch.complex64, device="cuda")
+            data.append((pts, c, f))
+        total_pts = sum(sp["M"] * sp["ntransf"] for sp in specs)
+
+        def make_plans(opts_for):
+            plans = []
+            for sp, (pts, c, f) in zip(specs, data):
+                kw = opts_for(sp)
+                p = binding.Plan(sp["type"], sp["N"], eps, prec=0, ntransf=sp["ntransf"],
+                                 stream=stream, **kw)
+                p.setpts(*pts)
+                plans.append(p)
+            return plans
+
+        def time_it(fn, steps):
+            for _ in range(args.warmup):
+                fn()
+            stream.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                fn()
+            b.record(stream)
+            b.synchronize()
+            return a.elapsed_time(b) / steps
+
+        # heuristic tiles, one plan after another
+        heur = make_plans(lambda sp: {})
+
+        def one_by_one(plans):
+            def run():
+                for p, (pts, c, f) in zip(plans, data):
+                    p.execute(c=c, f=f)
+            return run
+        ms_heur = time_it(one_by_one(heur), args.steps)
+        for p in heur:
+            p.close()
+
+        # autotune one representative per (type, dim) class and the ntransf plan
+        tuned = {}
+        t0 = time.perf_counter()
+        for key in sorted({(sp["type"], len(sp["N"]), sp["ntransf"]) for sp in specs}):
+            idx = [i for i, sp in enumerate(specs)
+                   if (sp["type"], len(sp["N"]), sp["ntransf"]) == key]
+            idx.sort(key=lambda i: specs[i]["M"] * max(specs[i]["N"]))
+            i = idx[len(idx) // 2]
+            sp = specs[i]
+            pts, c, f = data[i]
+            best, best_ms, _ = binding.autotune(sp["type"], sp["N"], eps, sp["M"], pts[0], pts[1],
+                                                pts[2] if len(pts) == 3 else None, c.clone(),
+                                                f.clone(), ntransf=sp["ntransf"], prec=0, reps=2,
+                                                stream=stream)
+            tuned[key] = dict(method=best.method, bins=tuple(best.bin)[: len(sp["N"])],
+                              msub=best.msub, threads=best.threads)
+        tune_s = time.perf_counter() - t0
+        plans = make_plans(lambda sp: tuned[(sp["type"], len(sp["N"]), sp["ntransf"])])
+        ms_tuned = time_it(one_by_one(plans), args.steps)
+        batch = binding.Batch(plans, stream=stream)
+        cs = [d[1] for d in data]
+        fs = [d[2] for d in data]
+        ms_batch = time_it(lambda: batch.execute(cs, fs), args.steps)
+        launches0 = binding.get_launch_count()
+        batch.capture(cs, fs)
+        graph_launches = binding.get_launch_count() - launches0
+        ms_graph = time_it(batch.launch, args.steps)
+        batch.close()
+        for p in plans:
+            p.close()
+    value = total_pts / (ms_graph / 1e3)
+    return {
+        "metric": "aggregate NU points/sec, 256 uneven plans + ntransf=32 plan, batched",
+        "value": round(value, 1), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_graph, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded SplitMix64 uniform points, N(0,1) strengths / modes)",
+        "config": {"workload": "batch-256: 128 2D (N in [32,512]^2) + 128 3D (N in [16,128]^3) "
+                               "plans, half type 1 / half type 2, M log-uniform in [1e4, 2e6], "
+                               "+ 2D 512^2 M=1e6 ntransf=32; eps=1e-5 complex64; execute only "
+                               "(points set once)",
+                   "tuned_tiles": {"%d-%dd-nt%d" % k: v for k, v in tuned.items()},
+                   "autotune_seconds": round(tune_s, 2)},
+        "arms_ms_per_step": {"one_by_one_heuristic": round(ms_heur, 4),
+                             "one_by_one_autotuned": round(ms_tuned, 4),
+                             "batched_execute": round(ms_batch, 4),
+                             "batched_graph": round(ms_graph, 4)},
+        "speedup_vs_one_by_one_heuristic": round(ms_heur / ms_graph, 3),
+        "total_points_per_step": int(total_pts),
+        "gpu_launches": int(graph_launches) * args.steps,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch-256"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--method1", default="auto")
     ap.add_argument("--method2", default="auto")
@@ -507,6 +643,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "batch-256":
+        print(json.dumps(run_batch_bench(args)), flush=True)
+        return
     W = dict(WORKLOADS[args.workload])
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -153,6 +153,38 @@ int nufft_get_sort(nufft_plan plan, int32_t *t, int32_t *bincounts, int32_t *nsu
    all threads).  cuFFT's own kernels are not counted. */
 uint64_t nufft_get_launch_count(void);
 
+/* ---- autotuner ----
+ * The paper hand-tunes its tiles for its own GPU (Sec. 4.1 remark).  This times
+ * candidate tiles -- method (SM, GM-sort, GM), bin sizes, M_sub and threads per
+ * CTA -- for one problem on the caller's data and returns the fastest execute.
+ *   type ... prec, base   as nufft_makeplan (base may be NULL; its stream is used).
+ *   M, x, y, z            points (device), M >= 1.
+ *   c, f                  device arrays of the plan's shapes; overwritten.
+ *   reps                  timed executes per candidate (median taken), >= 1.
+ *   best                  receives base with the winning method / bin / msub / threads.
+ *   best_ms               receives the winner's execute time (may be NULL).
+ *   trials, max_trials    optional per-candidate records; ntrials receives their count.
+ * The winner is also stored in a process-wide cache under the problem class
+ * (type, dim, precision, w, sigma, log2 fine-grid size, half-octave of M / n_tot);
+ * plans made with all tile options left automatic adopt cached tiles at setpts.
+ * Blocks the host until the timing is done. */
+typedef struct {
+    int    method;
+    int    bin[3];
+    int    msub;
+    int    threads;
+    double exec_ms;      /* median execute time */
+    double setpts_ms;    /* one setpts */
+} nufft_tune_trial;
+int nufft_autotune(int type, int dim, const int64_t *nmodes, int iflag, int ntransf, double eps,
+                   int prec, const nufft_opts *base, int64_t M, const void *x, const void *y,
+                   const void *z, void *c, void *f, int reps, nufft_opts *best, double *best_ms,
+                   nufft_tune_trial *trials, int max_trials, int *ntrials);
+/* Save / load the tuning cache as text (one class per line); clear it. */
+int nufft_tune_cache_save(const char *path);
+int nufft_tune_cache_load(const char *path);
+int nufft_tune_cache_clear(void);
+
 /* ---- batched execution of many plans ----
  * Not in the paper (its interface runs one plan at a time); for workloads of
  * many independent transforms of uneven N and M.  Plans that share type,

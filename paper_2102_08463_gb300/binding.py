@@ -34,7 +34,8 @@ EXPORTS = (
     "nufft_precorrect", "nufft_get_params", "nufft_get_finegrid", "nufft_get_sort",
     "nufft_spread_add", "nufft_get_launch_count", "nufft_binsort_noalloc",
     "nufft_batch_create", "nufft_batch_execute", "nufft_batch_capture", "nufft_batch_launch",
-    "nufft_batch_destroy",
+    "nufft_batch_destroy", "nufft_autotune", "nufft_tune_cache_save", "nufft_tune_cache_load",
+    "nufft_tune_cache_clear",
 )
 
 
@@ -42,6 +43,17 @@ class NufftError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
         super().__init__("%s failed: %s (%d)" % (where, strerror(code), code))
+
+
+class TuneTrial(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int),
+        ("bin", ctypes.c_int * 3),
+        ("msub", ctypes.c_int),
+        ("threads", ctypes.c_int),
+        ("exec_ms", ctypes.c_double),
+        ("setpts_ms", ctypes.c_double),
+    ]
 
 
 class Opts(ctypes.Structure):
@@ -99,6 +111,13 @@ def load():
         lib.nufft_get_sort.argtypes = [P, P, P, P]
         lib.nufft_spread_add.argtypes = [P, P]
         lib.nufft_get_launch_count.argtypes = []
+        lib.nufft_autotune.argtypes = [I, I, ctypes.POINTER(I64), I, I, ctypes.c_double, I,
+                                       ctypes.POINTER(Opts), I64, P, P, P, P, P, I,
+                                       ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(TuneTrial), I, ctypes.POINTER(I)]
+        lib.nufft_tune_cache_save.argtypes = [ctypes.c_char_p]
+        lib.nufft_tune_cache_load.argtypes = [ctypes.c_char_p]
+        lib.nufft_tune_cache_clear.argtypes = []
         lib.nufft_batch_create.argtypes = [ctypes.POINTER(P), I, P, ctypes.POINTER(P)]
         lib.nufft_batch_execute.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P)]
         lib.nufft_batch_capture.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P)]
@@ -184,6 +203,41 @@ def binsort_noalloc(dim, prec, M, x, y, z, nf, bins, perm, bincount, stream=None
     ba = (ctypes.c_int * 3)(*([int(v) for v in bins] + [1] * (3 - len(bins))))
     _check(load().nufft_binsort_noalloc(int(dim), int(prec), int(M), x, y, z, nfa, ba, perm,
                                         bincount, stream), "nufft_binsort_noalloc")
+
+
+def autotune(type_, N, eps, M, x, y, z, c, f, iflag=+1, ntransf=1, prec=-1, reps=3,
+             base=None, stream=None, max_trials=256):
+    """nufft_autotune on torch tensors; returns (best Opts, best_ms, list of trial dicts)."""
+    import torch
+    lib = load()
+    o = base if base is not None else default_opts()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o.stream = ctypes.c_void_p(stream.cuda_stream)
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in N] + [1] * (3 - len(N))))
+    best = Opts()
+    ms = ctypes.c_double()
+    trials = (TuneTrial * max_trials)()
+    nt = ctypes.c_int()
+    _check(lib.nufft_autotune(int(type_), len(N), arr, int(iflag), int(ntransf), float(eps),
+                              int(prec), ctypes.byref(o), int(M), _dptr(x), _dptr(y), _dptr(z),
+                              _dptr(c), _dptr(f), int(reps), ctypes.byref(best), ctypes.byref(ms),
+                              trials, max_trials, ctypes.byref(nt)), "nufft_autotune")
+    out = [dict(method=t.method, bin=tuple(t.bin), msub=t.msub, threads=t.threads,
+                exec_ms=t.exec_ms, setpts_ms=t.setpts_ms) for t in trials[: nt.value]]
+    return best, ms.value, out
+
+
+def tune_cache_save(path):
+    _check(load().nufft_tune_cache_save(str(path).encode()), "nufft_tune_cache_save")
+
+
+def tune_cache_load(path):
+    _check(load().nufft_tune_cache_load(str(path).encode()), "nufft_tune_cache_load")
+
+
+def tune_cache_clear():
+    _check(load().nufft_tune_cache_clear(), "nufft_tune_cache_clear")
 
 
 class Batch:

@@ -186,7 +186,21 @@ struct Plan {
     int32_t *scan_tmp = nullptr;   // [nbins] subproblem offsets per bin
     int smem_optin = 0;            // max dynamic shared memory per CTA (bytes)
     int smem_per_sm = 0;           // shared memory per SM (bytes)
+    bool auto_tiles = false;       // method, bins and msub left to the library
 };
+
+// Tile settings of a plan (method, bin sizes, subproblem cap, threads per CTA).
+struct Tiles {
+    int method = NUFFT_METHOD_SM;
+    int bin[3] = {1, 1, 1};
+    int msub = 1024;
+    int threads = 256;
+};
+// Re-tile an existing plan (keeps its cuFFT plan and fine grid); the points
+// must be set again afterwards.  Returns an NUFFT_ERR_* code.
+int plan_set_tiles(Plan &p, const Tiles &t);
+// Tuned tiles for this plan and M from the autotuner's cache, if any.
+bool tune_cache_lookup(const Plan &p, int64_t M, Tiles *out);
 
 // Launchers implemented in the .cu files.  All enqueue on p.stream and return a
 // cudaError_t from the last launch.

@@ -149,6 +149,45 @@ int default_method(const Plan &p, size_t smem_limit)
 
 }  // namespace
 
+int nufft::plan_set_tiles(Plan &p, const Tiles &t)
+{
+    if (t.method < NUFFT_METHOD_GM || t.method > NUFFT_METHOD_SM) return NUFFT_ERR_ARG;
+    if (t.msub < 1 || t.threads < 32 || t.threads > 256 || t.threads % 32) return NUFFT_ERR_ARG;
+    int m[3] = {1, 1, 1}, nb[3] = {1, 1, 1};
+    size_t cells = 1;
+    for (int d = 0; d < p.dim; ++d) {
+        if (t.bin[d] < 1) return NUFFT_ERR_ARG;
+        m[d] = t.bin[d] > p.nf[d] ? (int)p.nf[d] : t.bin[d];
+        if (padded(m[d], p.w) > 1023) return NUFFT_ERR_ARG;
+        nb[d] = (int)((p.nf[d] + m[d] - 1) / m[d]);
+        cells *= (size_t)padded(m[d], p.w);
+    }
+    if (t.method == NUFFT_METHOD_SM && cells * 2 * real_size(p) > (size_t)p.smem_optin)
+        return NUFFT_ERR_METHOD;
+    const int64_t nbins = (int64_t)nb[0] * nb[1] * nb[2];
+    if (nbins != p.nbins) {
+        dev_free(p.bincount);
+        dev_free(p.binstart);
+        dev_free(p.scan_tmp);
+        p.bincount = p.binstart = p.scan_tmp = nullptr;
+        int rc = dev_alloc(&p.bincount, sizeof(int32_t) * nbins);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.binstart, sizeof(int32_t) * nbins);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.scan_tmp, sizeof(int32_t) * nbins);
+        if (rc != NUFFT_OK) return rc;
+    }
+    for (int d = 0; d < 3; ++d) {
+        p.m[d] = m[d];
+        p.nb[d] = nb[d];
+    }
+    p.nbins = nbins;
+    p.method = t.method;
+    p.msub = t.msub;
+    p.threads = t.threads;
+    p.maxsub = 0;                   // the subproblem list is resized by the next setpts
+    p.have_pts = false;
+    return NUFFT_OK;
+}
+
 extern "C" {
 
 void nufft_default_opts(nufft_opts *o)
@@ -261,6 +300,8 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     if (p.nbins > ((int64_t)1 << 30)) { delete h; return NUFFT_ERR_SIZE; }
 
     p.method = o.method == NUFFT_METHOD_AUTO ? default_method(p, (size_t)smem_optin) : o.method;
+    p.auto_tiles = o.method == NUFFT_METHOD_AUTO && o.bin[0] == 0 && o.bin[1] == 0 &&
+                   o.bin[2] == 0 && o.msub == 0 && o.threads == 0;
     if (p.method == NUFFT_METHOD_SM) {
         size_t cells = 1;
         for (int d = 0; d < dim; ++d) cells *= (size_t)padded(p.m[d], w);
@@ -349,6 +390,15 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
     if (M < 0 || M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_ARG;
     if (M > 0 && (!x || !y || (p.dim == 3 && !z))) return NUFFT_ERR_ARG;
     p.have_pts = false;
+    if (p.auto_tiles) {
+        Tiles t;
+        if (tune_cache_lookup(p, M, &t) &&
+            (t.method != p.method || t.msub != p.msub || t.threads != p.threads ||
+             t.bin[0] != p.m[0] || t.bin[1] != p.m[1] || t.bin[2] != p.m[2])) {
+            const int rc = plan_set_tiles(p, t);
+            if (rc != NUFFT_OK) return rc;
+        }
+    }
     const int64_t maxsub = p.nbins + M / p.msub + 1;
     if (M > p.Mcap || maxsub > p.maxsub) {
         free_points(p);
