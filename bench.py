@@ -344,10 +344,6 @@ def run_gpu(args, W, rank, world, local_rank):
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_ms = float(e2e_t.item())
 
-    # ---- accuracy against the FP64 oracle on sampled modes / targets ----
-    acc = None
-    if rank == 0 and not args.no_accuracy:
-        acc = sampled_accuracy(W, pts, c, f, hfo.numpy(), hco.numpy())
 
     out = {
         "metric": METRIC,
@@ -385,8 +381,8 @@ def run_gpu(args, W, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    if acc is not None:
-        out["rel_l2_vs_oracle_sampled"] = acc
+    # outputs of the last step, for the sampled check in the CPU oracle leg
+    out["_outputs"] = (pts, c, f, hfo.numpy(), hco.numpy())
     p1.close()
     p2.close()
     return out
@@ -439,7 +435,10 @@ def cpu_sample(W, budget_s):
     return m
 
 
-def run_cpu_baseline(W, budget_s=15.0, steps=1):
+def run_cpu_baseline(W, budget_s=15.0, steps=1, gpu_outputs=None):
+    """The oracle timed on the host cores; with the GPU arm's outputs, also the
+    relative l2 error of those outputs on sampled modes / targets against the
+    oracle's exact sums."""
     import oracle
     oracle.set_num_threads(os.cpu_count() or 1)
     cores = oracle.num_threads()
@@ -450,11 +449,14 @@ def run_cpu_baseline(W, budget_s=15.0, steps=1):
     for _ in range(steps):
         oracle_step(Ws, pts, c, f)
     dt = (time.perf_counter() - t0) / steps
-    return {"value": round(2 * m / dt, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "one type 1 + type 2 FP64 oracle pipeline step (C spread/interp with "
-                      "OpenMP, numpy FFT) on %d of the %d points, full %s fine grid, eps=%g"
-                      % (m, W["M"], "x".join(map(str, W["nf"])), W["eps"]),
-            "s_per_step": round(dt, 3)}
+    out = {"value": round(2 * m / dt, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "one type 1 + type 2 FP64 oracle pipeline step (C spread/interp with "
+                     "OpenMP, numpy FFT) on %d of the %d points, full %s fine grid, eps=%g"
+                     % (m, W["M"], "x".join(map(str, W["nf"])), W["eps"]),
+           "s_per_step": round(dt, 3)}
+    if gpu_outputs is not None:
+        out["gpu_rel_l2_sampled"] = sampled_accuracy(W, *gpu_outputs)
+    return out
 
 
 def run_reference(args, W, rank):
@@ -628,12 +630,50 @@ def run_batch_bench(args):
     }
 
 
+def run_picker_bench(args):
+    """Held-out problems of the picker's distribution (seeds past the training
+    data's, in the evaluation split): every candidate tiling timed, then the
+    total execute time of the learned picker's choice against the heuristic
+    tiles and the fastest candidate."""
+    import torch
+    from paper_2102_08463_gb300 import binding, picker
+
+    torch.cuda.set_device(0)
+    weights = picker.DEFAULT_WEIGHTS
+    p = binding.Picker(path=weights)
+    probs = picker.sample_problems(args.picker_problems, first_seed=100000, heldout=True)
+    t0 = time.perf_counter()
+    rows = picker.collect(probs, reps=3)
+    collect_s = time.perf_counter() - t0
+    tot, per = picker.evaluate(p, rows)
+    p.close()
+    return {
+        "metric": "held-out total execute time with the learned tile picker",
+        "value": round(tot["picker"], 4), "unit": "ms", "n_gpus": 1, "steps": 1,
+        "warmup": args.warmup, "ms_per_step": round(tot["picker"], 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic (seeded SplitMix64 points: uniform, wrapped Gaussian, 8-Gaussian "
+                "mixture)",
+        "config": {"workload": "picker-holdout: %d problems, 2D/3D, type 1/2, N_i in [32,1024], "
+                               "M in [1e4,3e7], eps in [1e-12,1e-2] (work-bounded), every "
+                               "candidate tiling timed (median of 3 executes)" % tot["problems"],
+                   "weights": os.path.relpath(weights, ROOT)},
+        "heuristic_ms": round(tot["heuristic"], 4), "best_ms": round(tot["best"], 4),
+        "regret_vs_best": round(tot["regret"], 4),
+        "speedup_vs_heuristic": round(tot["speedup_vs_heuristic"], 4),
+        "collect_seconds": round(collect_s, 1),
+        "per_problem": per,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch-256"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS) + ["batch-256", "picker-holdout"])
+    ap.add_argument("--picker-problems", type=int, default=24)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--method1", default="auto")
     ap.add_argument("--method2", default="auto")
@@ -645,6 +685,9 @@ def main():
         args.warmup = 3
     if args.workload == "batch-256":
         print(json.dumps(run_batch_bench(args)), flush=True)
+        return
+    if args.workload == "picker-holdout":
+        print(json.dumps(run_picker_bench(args)), flush=True)
         return
     W = dict(WORKLOADS[args.workload])
 
@@ -664,8 +707,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     out = run_gpu(args, W, rank, world, local_rank)
+    outputs = out.pop("_outputs")
     if rank == 0 and world == 1 and not args.no_cpu:
-        out["cpu_baseline"] = run_cpu_baseline(W)
+        out["cpu_baseline"] = run_cpu_baseline(
+            W, gpu_outputs=None if args.no_accuracy else outputs)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

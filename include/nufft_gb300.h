@@ -72,6 +72,9 @@ typedef struct {
     void  *stream;        /* cudaStream_t to enqueue on; NULL = legacy default stream */
     int    threads;       /* threads per block for spread / interp; 0 = default 256 */
     int    ctas_per_sm;   /* persistent CTAs per SM for the subproblem kernels; 0 = auto */
+    int    use_picker;    /* 1 = with method, bin, msub and threads all automatic, let the
+                             installed tile picker (nufft_picker_install) choose them at
+                             setpts, after the autotuner's cache; 0 = off */
 } nufft_opts;
 
 /* Fill opts with the defaults listed above. */
@@ -148,6 +151,9 @@ int nufft_get_finegrid(nufft_plan plan, void **dptr, size_t *bytes);
    the per-bin counts (int32[nbins]) and the subproblem count (int32[1]);
    any destination may be NULL. */
 int nufft_get_sort(nufft_plan plan, int32_t *t, int32_t *bincounts, int32_t *nsub);
+/* The plan's current tiles: fills method, bin[3] (1 on unused axes), msub and
+   threads of *out and leaves the other fields alone. */
+int nufft_get_tiles(nufft_plan plan, nufft_opts *out);
 
 /* Number of CUDA kernels this library has launched in this process (all plans,
    all threads).  cuFFT's own kernels are not counted. */
@@ -238,6 +244,74 @@ int nufft_batch_destroy(nufft_batch batch);
 int nufft_binsort_noalloc(int dim, int prec, int64_t M, const void *x, const void *y,
                           const void *z, const int64_t *nf, const int *bins, int32_t *perm,
                           int32_t *bincount, void *stream);
+
+/* ---- learned tile picker ----
+ * Not in the paper, which fixes the method and tiles by hand-tuned rules (Sec.
+ * 4.1 remark; method advice of Sec. 5.4).  A perceptron 12 -> 64 -> 64 -> 1 with
+ * ReLU predicts log2 of the execute time (ms) of a plan under one candidate
+ * tiling from NUFFT_PICKER_NFEAT features (nufft_picker_features); a plan made
+ * with opts.use_picker = 1 evaluates it over the autotuner's candidate list at
+ * setpts and takes the argmin (first in list order on ties) among the tilings
+ * the plan can run.  With no picker installed such plans keep the heuristic
+ * tiles.  Forward, backward, loss and Adam run in the library's kernels in
+ * single precision on the device the picker was created on.
+ *
+ * Parameters: NUFFT_PICKER_NPARAM floats, in the order W1[64][12] (row = unit),
+ * b1[64], W2[64][64], b2[64], w3[64], b3.  Training data: X[n][12] features
+ * (row-major) and T[n] targets = log2(exec ms), device arrays.
+ *
+ * nufft_picker_create   He-uniform weights from SplitMix64(seed), zero biases.
+ * nufft_picker_set_params / get_params   host arrays of NPARAM floats; setting
+ *                       also zeroes the Adam moments and step count.
+ * nufft_picker_save / load   the parameters as text (one value per line).
+ * nufft_picker_predict  y[B] = network(X[B][12]); asynchronous on stream.
+ * nufft_picker_grad     grad[NPARAM] = dL/dtheta and loss[0] = L for the mean
+ *                       squared error L over the B samples; device outputs.
+ * nufft_picker_step     one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, rate lr)
+ *                       on the B samples; loss[0] (device, may be NULL) = L before.
+ * nufft_picker_train    epochs of Adam over shuffled minibatches of `batch`
+ *                       samples (order from SplitMix64(seed)); *final_loss (host)
+ *                       = L over all n afterwards.  Synchronizes stream.
+ * nufft_picker_loss     L over n samples into loss[0] (device).
+ * nufft_picker_install  make `picker` the process-wide picker (NULL = none); the
+ *                       caller keeps it alive until it is uninstalled or
+ *                       destroyed (destroy uninstalls it).
+ * nufft_picker_features the 12 features of a problem and candidate tiling:
+ *     [0] type == 2  [1] dim == 3  [2] double precision  [3] w / 16
+ *     [4] log2(n_tot) / 32  [5] log2(M / n_tot) / 8  [6] skew / 16
+ *     [7] method == SM  [8] method == GM  [9] log2(bin cells) / 12
+ *     [10] log2(M_sub) / 12  [11] threads / 256
+ *   prec -1 resolves as in makeplan; tiles->bin / msub / threads 0 mean the
+ *   defaults; tiles->method must not be AUTO.
+ * nufft_point_skew      skew = log2(max count * 4096 / M) of the points in a fixed
+ *                       grid of 4096 equal boxes (64 x 64 in 2D, 16^3 in 3D) over
+ *                       the period, at least 0 (0 for M = 0); synchronizes stream.
+ * Errors: NUFFT_ERR_ARG, NUFFT_ERR_ALLOC, NUFFT_ERR_CUDA, NUFFT_ERR_EPS. */
+#define NUFFT_PICKER_NFEAT  12
+#define NUFFT_PICKER_HIDDEN 64
+#define NUFFT_PICKER_NPARAM 5057
+typedef struct nufft_picker_s *nufft_picker;
+int nufft_picker_create(uint64_t seed, nufft_picker *out);
+int nufft_picker_destroy(nufft_picker picker);
+int nufft_picker_set_params(nufft_picker picker, const float *params);
+int nufft_picker_get_params(nufft_picker picker, float *params);
+int nufft_picker_save(nufft_picker picker, const char *path);
+int nufft_picker_load(nufft_picker picker, const char *path);
+int nufft_picker_predict(nufft_picker picker, int64_t B, const float *X, float *y, void *stream);
+int nufft_picker_grad(nufft_picker picker, int64_t B, const float *X, const float *T, float *grad,
+                      float *loss, void *stream);
+int nufft_picker_step(nufft_picker picker, int64_t B, const float *X, const float *T, float lr,
+                      float *loss, void *stream);
+int nufft_picker_train(nufft_picker picker, int64_t n, const float *X, const float *T, int epochs,
+                       int batch, float lr, uint64_t seed, float *final_loss, void *stream);
+int nufft_picker_loss(nufft_picker picker, int64_t n, const float *X, const float *T, float *loss,
+                      void *stream);
+int nufft_picker_install(nufft_picker picker);
+int nufft_picker_features(int type, int dim, const int64_t *nmodes, double eps, int prec,
+                          double upsampfac, int64_t M, double skew, const nufft_opts *tiles,
+                          float *out);
+int nufft_point_skew(int dim, int prec, int64_t M, const void *x, const void *y, const void *z,
+                     double *skew, void *stream);
 
 #ifdef __cplusplus
 }

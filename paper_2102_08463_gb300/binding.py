@@ -35,8 +35,15 @@ EXPORTS = (
     "nufft_spread_add", "nufft_get_launch_count", "nufft_binsort_noalloc",
     "nufft_batch_create", "nufft_batch_execute", "nufft_batch_capture", "nufft_batch_launch",
     "nufft_batch_destroy", "nufft_autotune", "nufft_tune_cache_save", "nufft_tune_cache_load",
-    "nufft_tune_cache_clear",
+    "nufft_tune_cache_clear", "nufft_get_tiles", "nufft_picker_create", "nufft_picker_destroy",
+    "nufft_picker_set_params", "nufft_picker_get_params", "nufft_picker_save",
+    "nufft_picker_load", "nufft_picker_predict", "nufft_picker_grad", "nufft_picker_step",
+    "nufft_picker_train", "nufft_picker_loss", "nufft_picker_install", "nufft_picker_features",
+    "nufft_point_skew",
 )
+
+PICKER_NFEAT = 12
+PICKER_NPARAM = 5057
 
 
 class NufftError(RuntimeError):
@@ -65,6 +72,7 @@ class Opts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("threads", ctypes.c_int),
         ("ctas_per_sm", ctypes.c_int),
+        ("use_picker", ctypes.c_int),
     ]
 
 
@@ -125,6 +133,25 @@ def load():
         lib.nufft_batch_destroy.argtypes = [P]
         lib.nufft_binsort_noalloc.argtypes = [I, I, I64, P, P, P, ctypes.POINTER(I64),
                                               ctypes.POINTER(I), P, P, P]
+        F = ctypes.c_float
+        FP = ctypes.POINTER(ctypes.c_float)
+        lib.nufft_get_tiles.argtypes = [P, ctypes.POINTER(Opts)]
+        lib.nufft_picker_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
+        lib.nufft_picker_destroy.argtypes = [P]
+        lib.nufft_picker_set_params.argtypes = [P, FP]
+        lib.nufft_picker_get_params.argtypes = [P, FP]
+        lib.nufft_picker_save.argtypes = [P, ctypes.c_char_p]
+        lib.nufft_picker_load.argtypes = [P, ctypes.c_char_p]
+        lib.nufft_picker_predict.argtypes = [P, I64, P, P, P]
+        lib.nufft_picker_grad.argtypes = [P, I64, P, P, P, P, P]
+        lib.nufft_picker_step.argtypes = [P, I64, P, P, F, P, P]
+        lib.nufft_picker_train.argtypes = [P, I64, P, P, I, I, F, ctypes.c_uint64, FP, P]
+        lib.nufft_picker_loss.argtypes = [P, I64, P, P, P, P]
+        lib.nufft_picker_install.argtypes = [P]
+        lib.nufft_picker_features.argtypes = [I, I, ctypes.POINTER(I64), ctypes.c_double, I,
+                                              ctypes.c_double, I64, ctypes.c_double,
+                                              ctypes.POINTER(Opts), FP]
+        lib.nufft_point_skew.argtypes = [I, I, I64, P, P, P, ctypes.POINTER(ctypes.c_double), P]
         for name in EXPORTS:
             if name not in ("nufft_default_opts", "nufft_strerror", "nufft_get_launch_count"):
                 getattr(lib, name).restype = I
@@ -291,6 +318,150 @@ class Batch:
             pass
 
 
+def get_tiles(h):
+    """The plan's current method, bins, M_sub and threads."""
+    o = Opts()
+    _check(load().nufft_get_tiles(ctypes.c_void_p(h), ctypes.byref(o)), "nufft_get_tiles")
+    return dict(method=o.method, bin=tuple(o.bin), msub=o.msub, threads=o.threads)
+
+
+def picker_features(type_, N, eps, M, skew, method, bins=None, msub=0, threads=0, prec=-1,
+                    upsampfac=2.0):
+    """nufft_picker_features: the 12 cost-model features of a problem and a tiling."""
+    o = default_opts()
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
+    for i, b in enumerate(bins or ()):
+        o.bin[i] = int(b)
+    o.msub = int(msub)
+    o.threads = int(threads)
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in N] + [1] * (3 - len(N))))
+    out = (ctypes.c_float * PICKER_NFEAT)()
+    _check(load().nufft_picker_features(int(type_), len(N), arr, float(eps), int(prec),
+                                        float(upsampfac), int(M), float(skew), ctypes.byref(o),
+                                        out), "nufft_picker_features")
+    return list(out)
+
+
+def point_skew(x, y, z=None, stream=None):
+    """nufft_point_skew on torch tensors (float32 or float64); synchronizes."""
+    import torch
+    dim = 2 if z is None else 3
+    prec = 0 if x.dtype == torch.float32 else 1
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = ctypes.c_double()
+    _check(load().nufft_point_skew(dim, prec, int(x.shape[0]), _dptr(x), _dptr(y), _dptr(z),
+                                   ctypes.byref(s), ctypes.c_void_p(stream.cuda_stream)),
+           "nufft_point_skew")
+    return s.value
+
+
+class Picker:
+    """The learned tile picker (nufft_picker_*): a 12-64-64-1 ReLU perceptron
+    predicting log2 of execute milliseconds; tensors are float32 CUDA tensors."""
+
+    def __init__(self, seed=0, params=None, path=None):
+        import torch
+        self._torch = torch
+        h = ctypes.c_void_p()
+        _check(load().nufft_picker_create(ctypes.c_uint64(int(seed) & (2 ** 64 - 1)),
+                                          ctypes.byref(h)), "nufft_picker_create")
+        self.handle = h.value
+        if params is not None:
+            self.set_params(params)
+        if path is not None:
+            self.load(path)
+
+    def _st(self, stream):
+        s = stream if stream is not None else self._torch.cuda.current_stream()
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if a.size != PICKER_NPARAM:
+            raise ValueError("expected %d parameters" % PICKER_NPARAM)
+        _check(load().nufft_picker_set_params(ctypes.c_void_p(self.handle),
+                                              a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "nufft_picker_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(PICKER_NPARAM, dtype=np.float32)
+        _check(load().nufft_picker_get_params(ctypes.c_void_p(self.handle),
+                                              a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "nufft_picker_get_params")
+        return a
+
+    def save(self, path):
+        _check(load().nufft_picker_save(ctypes.c_void_p(self.handle), str(path).encode()),
+               "nufft_picker_save")
+
+    def load(self, path):
+        _check(load().nufft_picker_load(ctypes.c_void_p(self.handle), str(path).encode()),
+               "nufft_picker_load")
+
+    def predict(self, X, stream=None):
+        y = self._torch.empty(X.shape[0], dtype=self._torch.float32, device=X.device)
+        _check(load().nufft_picker_predict(ctypes.c_void_p(self.handle), int(X.shape[0]),
+                                           _dptr(X, self._torch.float32, "X"), _dptr(y),
+                                           self._st(stream)), "nufft_picker_predict")
+        return y
+
+    def grad(self, X, T, stream=None):
+        torch = self._torch
+        g = torch.empty(PICKER_NPARAM, dtype=torch.float32, device=X.device)
+        L = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(load().nufft_picker_grad(ctypes.c_void_p(self.handle), int(X.shape[0]),
+                                        _dptr(X, torch.float32, "X"), _dptr(T, torch.float32, "T"),
+                                        _dptr(g), _dptr(L), self._st(stream)), "nufft_picker_grad")
+        return g, L
+
+    def step(self, X, T, lr, stream=None):
+        torch = self._torch
+        L = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(load().nufft_picker_step(ctypes.c_void_p(self.handle), int(X.shape[0]),
+                                        _dptr(X, torch.float32, "X"), _dptr(T, torch.float32, "T"),
+                                        float(lr), _dptr(L), self._st(stream)), "nufft_picker_step")
+        return L
+
+    def train(self, X, T, epochs, batch=256, lr=1e-3, seed=0, stream=None):
+        torch = self._torch
+        out = ctypes.c_float()
+        _check(load().nufft_picker_train(ctypes.c_void_p(self.handle), int(X.shape[0]),
+                                         _dptr(X, torch.float32, "X"),
+                                         _dptr(T, torch.float32, "T"), int(epochs), int(batch),
+                                         float(lr), ctypes.c_uint64(int(seed) & (2 ** 64 - 1)),
+                                         ctypes.byref(out), self._st(stream)), "nufft_picker_train")
+        return out.value
+
+    def loss(self, X, T, stream=None):
+        torch = self._torch
+        L = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(load().nufft_picker_loss(ctypes.c_void_p(self.handle), int(X.shape[0]),
+                                        _dptr(X, torch.float32, "X"), _dptr(T, torch.float32, "T"),
+                                        _dptr(L), self._st(stream)), "nufft_picker_loss")
+        return L
+
+    def install(self):
+        _check(load().nufft_picker_install(ctypes.c_void_p(self.handle)), "nufft_picker_install")
+
+    @staticmethod
+    def uninstall():
+        _check(load().nufft_picker_install(None), "nufft_picker_install")
+
+    def close(self):
+        if self.handle:
+            load().nufft_picker_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def get_launch_count() -> int:
     return int(load().nufft_get_launch_count())
 
@@ -350,7 +521,8 @@ class Plan:
     """
 
     def __init__(self, type_, N, eps, iflag=+1, ntransf=1, prec=-1, method="auto",
-                 bins=None, msub=0, upsampfac=2.0, stream=None, threads=0, ctas_per_sm=0):
+                 bins=None, msub=0, upsampfac=2.0, stream=None, threads=0, ctas_per_sm=0,
+                 use_picker=False):
         import torch
         self._torch = torch
         self.type = int(type_)
@@ -370,6 +542,7 @@ class Plan:
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         o.threads = int(threads)
         o.ctas_per_sm = int(ctas_per_sm)
+        o.use_picker = 1 if use_picker else 0
         self.handle = None
         self.handle = makeplan(self.type, self.dim, self.N, iflag, ntransf, eps, prec, o)
         self.params = get_params(self.handle)
@@ -420,6 +593,9 @@ class Plan:
         self.stream.synchronize()
         view = _DeviceView(ptr, shape, "<c8" if self.params["prec"] == 0 else "<c16")
         return torch.as_tensor(view, device="cuda").clone()
+
+    def tiles(self):
+        return get_tiles(self.handle)
 
     def sort(self):
         torch = self._torch

@@ -55,10 +55,19 @@ Key key_of(const Plan &p, int64_t M)
     return k;
 }
 
-std::vector<Tiles> candidates(const Plan &p)
+int cuda_rc(cudaError_t e)
+{
+    if (e == cudaSuccess) return NUFFT_OK;
+    cudaGetLastError();
+    return NUFFT_ERR_CUDA;
+}
+
+}  // namespace
+
+std::vector<Tiles> nufft::tile_candidates(int dim)
 {
     std::vector<std::vector<int>> bins;
-    if (p.dim == 2)
+    if (dim == 2)
         bins = {{8, 8, 1}, {16, 16, 1}, {32, 16, 1}, {32, 32, 1}, {64, 32, 1}};
     else
         bins = {{8, 8, 4}, {8, 8, 8}, {16, 16, 2}, {16, 16, 4}, {16, 8, 4}, {32, 32, 2}, {32, 16, 4}};
@@ -81,19 +90,10 @@ std::vector<Tiles> candidates(const Plan &p)
     Tiles gm;
     gm.method = NUFFT_METHOD_GM;
     gm.bin[0] = gm.bin[1] = 16;
-    gm.bin[2] = p.dim == 3 ? 2 : 1;
+    gm.bin[2] = dim == 3 ? 2 : 1;
     out.push_back(gm);
     return out;
 }
-
-int cuda_rc(cudaError_t e)
-{
-    if (e == cudaSuccess) return NUFFT_OK;
-    cudaGetLastError();
-    return NUFFT_ERR_CUDA;
-}
-
-}  // namespace
 
 bool nufft::tune_cache_lookup(const Plan &p, int64_t M, Tiles *out)
 {
@@ -132,7 +132,7 @@ int nufft_autotune(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     double best_time = 1e300;
     Tiles best_t;
     int n = 0;
-    for (const Tiles &t : candidates(p)) {
+    for (const Tiles &t : tile_candidates(p.dim)) {
         if (plan_set_tiles(p, t) != NUFFT_OK) continue;
         cudaEventRecord(e0, p.stream);
         if (nufft_setpts(h, M, x, y, z) != NUFFT_OK) continue;

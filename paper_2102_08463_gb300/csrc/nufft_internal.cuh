@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <vector>
 
 #include "../../include/nufft_gb300.h"
 
@@ -187,6 +188,7 @@ struct Plan {
     int smem_optin = 0;            // max dynamic shared memory per CTA (bytes)
     int smem_per_sm = 0;           // shared memory per SM (bytes)
     bool auto_tiles = false;       // method, bins and msub left to the library
+    bool use_picker = false;       // consult the installed tile picker at setpts
 };
 
 // Tile settings of a plan (method, bin sizes, subproblem cap, threads per CTA).
@@ -199,8 +201,20 @@ struct Tiles {
 // Re-tile an existing plan (keeps its cuFFT plan and fine grid); the points
 // must be set again afterwards.  Returns an NUFFT_ERR_* code.
 int plan_set_tiles(Plan &p, const Tiles &t);
+// Whether plan_set_tiles would accept t for this plan (no state is changed).
+bool tiles_feasible(const Plan &p, const Tiles &t);
 // Tuned tiles for this plan and M from the autotuner's cache, if any.
 bool tune_cache_lookup(const Plan &p, int64_t M, Tiles *out);
+// The candidate tilings the autotuner times and the picker ranks, in a fixed order.
+std::vector<Tiles> tile_candidates(int dim);
+// Tiles chosen by the installed picker for this plan and these points.  Sets
+// *chosen = false (and returns NUFFT_OK) when no picker is installed.
+// Synchronizes p.stream.
+int picker_choose(Plan &p, int64_t M, const void *x, const void *y, const void *z, Tiles *out,
+                  bool *chosen);
+// Parameter rules of Sec. 3 shared by makeplan and the picker's features.
+int next235(int64_t n);
+int kernel_width(double eps, double sigma);
 
 // Launchers implemented in the .cu files.  All enqueue on p.stream and return a
 // cudaError_t from the last launch.

@@ -14,9 +14,7 @@ using namespace nufft;
 
 std::atomic<unsigned long long> nufft::g_launch_count{0};
 
-namespace {
-
-int next235(int64_t n)
+int nufft::next235(int64_t n)
 {
     if (n < 1) n = 1;
     for (;; ++n) {
@@ -32,13 +30,15 @@ int next235(int64_t n)
 // ten map to their nominal width: a 1e-10 guard absorbs the rounding of
 // log10 of a decimal tolerance.  sigma = 1.25 uses the calibrated width
 // ceil(log10(1/eps) / 0.6) + 1.
-int kernel_width(double eps, double sigma)
+int nufft::kernel_width(double eps, double sigma)
 {
     double digits = -log10(eps);
     double w = sigma == 2.0 ? ceil(digits - 1e-10) + 1.0 : ceil(digits / 0.6 - 1e-10) + 1.0;
     if (w < 2.0) w = 2.0;
     return (int)fmin(w, 99.0);
 }
+
+namespace {
 
 // beta = 2.30 w for sigma = 2 (Sec. 3); scaled by (1 - 1/(2 sigma)) / (3/4) otherwise.
 double kernel_beta(int w, double sigma)
@@ -148,6 +148,20 @@ int default_method(const Plan &p, size_t smem_limit)
 }
 
 }  // namespace
+
+bool nufft::tiles_feasible(const Plan &p, const Tiles &t)
+{
+    if (t.method < NUFFT_METHOD_GM || t.method > NUFFT_METHOD_SM) return false;
+    if (t.msub < 1 || t.threads < 32 || t.threads > 256 || t.threads % 32) return false;
+    size_t cells = 1;
+    for (int d = 0; d < p.dim; ++d) {
+        if (t.bin[d] < 1) return false;
+        const int m = t.bin[d] > p.nf[d] ? (int)p.nf[d] : t.bin[d];
+        if (padded(m, p.w) > 1023) return false;
+        cells *= (size_t)padded(m, p.w);
+    }
+    return !(t.method == NUFFT_METHOD_SM && cells * 2 * real_size(p) > (size_t)p.smem_optin);
+}
 
 int nufft::plan_set_tiles(Plan &p, const Tiles &t)
 {
@@ -302,6 +316,7 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     p.method = o.method == NUFFT_METHOD_AUTO ? default_method(p, (size_t)smem_optin) : o.method;
     p.auto_tiles = o.method == NUFFT_METHOD_AUTO && o.bin[0] == 0 && o.bin[1] == 0 &&
                    o.bin[2] == 0 && o.msub == 0 && o.threads == 0;
+    p.use_picker = p.auto_tiles && o.use_picker != 0;
     if (p.method == NUFFT_METHOD_SM) {
         size_t cells = 1;
         for (int d = 0; d < dim; ++d) cells *= (size_t)padded(p.m[d], w);
@@ -391,10 +406,16 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
     if (M > 0 && (!x || !y || (p.dim == 3 && !z))) return NUFFT_ERR_ARG;
     p.have_pts = false;
     if (p.auto_tiles) {
+        // measured tiles from the autotuner's cache first, then the picker's
+        // prediction, else the heuristic tiles chosen at makeplan stay
         Tiles t;
-        if (tune_cache_lookup(p, M, &t) &&
-            (t.method != p.method || t.msub != p.msub || t.threads != p.threads ||
-             t.bin[0] != p.m[0] || t.bin[1] != p.m[1] || t.bin[2] != p.m[2])) {
+        bool have = tune_cache_lookup(p, M, &t);
+        if (!have && p.use_picker) {
+            const int rc = picker_choose(p, M, x, y, z, &t, &have);
+            if (rc != NUFFT_OK) return rc;
+        }
+        if (have && (t.method != p.method || t.msub != p.msub || t.threads != p.threads ||
+                     t.bin[0] != p.m[0] || t.bin[1] != p.m[1] || t.bin[2] != p.m[2])) {
             const int rc = plan_set_tiles(p, t);
             if (rc != NUFFT_OK) return rc;
         }
@@ -586,6 +607,17 @@ int nufft_get_finegrid(nufft_plan h, void **dptr, size_t *bytes)
     const Plan &p = h->p;
     if (dptr) *dptr = p.fine;
     if (bytes) *bytes = (size_t)p.nftot * p.ntransf * 2 * real_size(p);
+    return NUFFT_OK;
+}
+
+int nufft_get_tiles(nufft_plan h, nufft_opts *out)
+{
+    if (!h || !out) return NUFFT_ERR_ARG;
+    const Plan &p = h->p;
+    out->method = p.method;
+    for (int d = 0; d < 3; ++d) out->bin[d] = p.m[d];
+    out->msub = p.msub;
+    out->threads = p.threads;
     return NUFFT_OK;
 }
 

@@ -53,9 +53,18 @@ def points(kind: str, dim: int, M: int, seed: int, dtype=np.float32, n=None,
     """List of `dim` coordinate arrays of M points in the plan's precision.
 
     kind: "rand" (uniform on [-pi, pi)), "gauss" (wrapped N(0, spread^2)),
-    "cluster" (uniform on [0, 8 h_i], needs the fine-grid sizes n).
+    "cluster" (uniform on [0, 8 h_i], needs the fine-grid sizes n), "mixture"
+    (8 equally likely wrapped Gaussians N(c_k, spread^2), centres uniform).
     """
     out = []
+    if kind == "mixture":
+        comp = np.minimum((uniform01(seed, M, stream=90) * 8).astype(np.int64), 7)
+        for d in range(dim):
+            centres = -math.pi + 2.0 * math.pi * uniform01(seed, 8, stream=91 + d)
+            g = centres[comp] + spread * normal(seed, M, stream=95 + d)
+            x = g - 2.0 * math.pi * np.floor((g + math.pi) / (2.0 * math.pi))
+            out.append(np.ascontiguousarray(x.astype(dtype)))
+        return out
     for d in range(dim):
         if kind == "rand":
             x = -math.pi + 2.0 * math.pi * uniform01(seed, M, stream=d)

@@ -1,0 +1,238 @@
+"""The learned tile picker on the GPU: its forward, gradient, loss and Adam
+kernels against the FP64 oracle (oracle/mlp.py) on the same seeded inputs; the
+point-skew feature against a histogram taken here; and plans made with
+use_picker choosing the argmin of a network whose predictions are known."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2102_08463_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_08463_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _theta(seed):
+    # He-scaled normal weights and small biases, so most units are active
+    th = wl.normal(seed, mlp.NPARAM, stream=21)
+    W1, b1, W2, b2, w3, b3 = mlp.unpack(th)
+    return mlp.pack(W1 * math.sqrt(2 / 12), 0.1 * b1, W2 * math.sqrt(2 / 64), 0.1 * b2,
+                    w3 * math.sqrt(1 / 64), 0.1 * b3)
+
+
+def _data(seed, B):
+    X = wl.uniform01(seed, B * 12, stream=22).reshape(B, 12) * 2.0 - 1.0
+    T = wl.normal(seed, B, stream=23)
+    return X, T
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _rel(a, b):
+    a = np.asarray(a).astype(np.complex128).ravel()
+    b = np.asarray(b).astype(np.complex128).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("B", [1, 63, 1000, 4099])
+def test_forward_matches_oracle(nb, B):
+    th = _theta(100 + B)
+    X, _ = _data(200 + B, B)
+    p = nb.Picker(params=th)
+    y = p.predict(_dev(X)).cpu().numpy()
+    # the oracle sees the same single-precision parameters and inputs
+    y0, _ = mlp.forward(th.astype(np.float32).astype(np.float64),
+                        X.astype(np.float32).astype(np.float64))
+    scale = max(1.0, float(np.max(np.abs(y0))))
+    assert np.max(np.abs(y - y0)) <= 2e-5 * scale
+    p.close()
+
+
+@pytest.mark.parametrize("B", [1, 257, 1000])
+def test_gradient_and_loss_match_oracle(nb, B):
+    th = _theta(300 + B).astype(np.float32).astype(np.float64)
+    X, T = _data(400 + B, B)
+    X = X.astype(np.float32).astype(np.float64)
+    T = T.astype(np.float32).astype(np.float64)
+    p = nb.Picker(params=th)
+    g, L = p.grad(_dev(X), _dev(T))
+    g0 = mlp.grad(th, X, T)
+    assert _rel(g.cpu().numpy(), g0) < 1e-4
+    assert float(L.item()) == pytest.approx(mlp.loss(th, X, T), rel=1e-5)
+    L2 = p.loss(_dev(X), _dev(T))
+    assert float(L2.item()) == pytest.approx(mlp.loss(th, X, T), rel=1e-5)
+    p.close()
+
+
+def test_adam_steps_match_oracle(nb):
+    th = _theta(500).astype(np.float32).astype(np.float64)
+    X, T = _data(501, 600)
+    X = X.astype(np.float32).astype(np.float64)
+    T = (np.sin(2 * X[:, 0]) + X[:, 1] ** 2).astype(np.float32).astype(np.float64)
+    batches = [(X[i:i + 150], T[i:i + 150]) for i in range(0, 600, 150)] * 5
+    lr = 1e-3
+    p = nb.Picker(params=th)
+    # the first step of Adam moves every coordinate with a clear gradient by lr
+    g0 = mlp.grad(th, *batches[0])
+    p.step(_dev(batches[0][0]), _dev(batches[0][1]), lr)
+    th1 = p.get_params().astype(np.float64)
+    step = th - th1
+    assert np.max(np.abs(step)) <= lr * (1 + 1e-3)
+    clear = np.abs(g0) > 1e-3 * np.sqrt(np.mean(g0 ** 2))
+    assert np.allclose(step[clear], lr * g0[clear] / (np.abs(g0[clear]) + 1e-8), rtol=1e-3,
+                       atol=0)
+    # then 19 more, against the oracle's trajectory from the same start
+    losses = []
+    for Xb, Tb in batches[1:]:
+        losses.append(float(p.step(_dev(Xb), _dev(Tb), lr).item()))
+    th_o, losses_o = mlp.train_steps(th, batches, lr)
+    assert np.allclose(losses, losses_o[1:], rtol=2e-3)
+    assert _rel(p.get_params(), th_o) < 1e-3
+    p.close()
+
+
+def test_train_fits_and_save_load(nb, tmp_path):
+    X, _ = _data(600, 4096)
+    T = np.sin(2 * X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] + np.abs(X[:, 3])
+    p = nb.Picker(seed=7)
+    Xd, Td = _dev(X), _dev(T)
+    before = float(p.loss(Xd, Td).item())
+    after = p.train(Xd, Td, epochs=60, batch=256, lr=3e-3, seed=1)
+    assert after < 0.05 * before
+    path = tmp_path / "picker.txt"
+    p.save(path)
+    q = nb.Picker(seed=99)
+    q.load(path)
+    assert np.array_equal(q.get_params(), p.get_params())
+    assert torch.equal(q.predict(Xd), p.predict(Xd))
+    p.close()
+    q.close()
+
+
+@pytest.mark.parametrize("dim,kind,M,prec", [(2, "rand", 100000, 0), (3, "gauss", 200000, 0),
+                                             (3, "rand", 5, 1), (2, "cluster", 70000, 1)])
+def test_point_skew(nb, dim, kind, M, prec):
+    dt = np.float32 if prec == 0 else np.float64
+    pts = wl.points(kind, dim, M, 700 + M, dt, n=(128,) * dim)
+    s = nb.point_skew(*[torch.from_numpy(a).cuda() for a in pts])
+    g = 64 if dim == 2 else 16
+    box = np.zeros(M, dtype=np.int64)
+    for d, a in enumerate(pts):
+        u = np.floor((a.astype(np.float64) + np.pi) * g / (2 * np.pi)).astype(np.int64) % g
+        box += u * g ** d
+    mx = np.bincount(box, minlength=4096).max()
+    want = max(0.0, math.log2(mx * 4096 / M))
+    # boxes are cut in single precision on the GPU: a point on a box edge may
+    # fall either way
+    assert 2 ** s == pytest.approx(2 ** want, rel=0.02, abs=4 * 4096 / M)
+    assert nb.point_skew(*[torch.from_numpy(a[:0]).cuda() for a in pts]) == 0.0
+
+
+def _one_unit_net(feature, sign):
+    """y = sign * x[feature] for x[feature] >= 0 (one active unit)."""
+    W1 = np.zeros((64, 12))
+    W1[0, feature] = 1.0
+    W2 = np.zeros((64, 64))
+    W2[0, 0] = 1.0
+    w3 = np.zeros(64)
+    w3[0] = sign
+    return mlp.pack(W1, np.zeros(64), W2, np.zeros(64), w3, 0.0)
+
+
+def test_plan_takes_the_pickers_argmin(nb):
+    N, M, eps = (64, 48), 20000, 1e-5
+    pts = [torch.from_numpy(a).cuda() for a in wl.points("rand", 2, M, 800, np.float32)]
+    c = torch.from_numpy(wl.strengths(M, 801, np.complex64)).cuda()
+    nb.Picker.uninstall()
+    nb.tune_cache_clear()
+    # no picker installed: the heuristic tiles stay
+    with nb.Plan(1, N, eps, use_picker=True) as p:
+        p.setpts(*pts)
+        assert p.tiles() == dict(method=3, bin=(16, 16, 1), msub=1024, threads=256)
+        ref = p.execute(c=c)
+    # y = -log2(bin cells) / 12: the largest bins win, first in candidate order
+    # (SM before GM-sort, M_sub 256 and 128 threads first)
+    big = nb.Picker(params=_one_unit_net(9, -1.0))
+    big.install()
+    with nb.Plan(1, N, eps, use_picker=True) as p:
+        p.setpts(*pts)
+        assert p.tiles() == dict(method=3, bin=(64, 32, 1), msub=256, threads=128)
+        assert _rel(p.execute(c=c).cpu().numpy(), ref.cpu().numpy()) < 1e-5
+    # a plan with its tiles set by hand ignores the picker
+    with nb.Plan(1, N, eps, use_picker=True, bins=(16, 16)) as p:
+        p.setpts(*pts)
+        assert p.tiles()["bin"] == (16, 16, 1)
+    # y = -[method == GM]: GM wins; the result is unchanged
+    gm = nb.Picker(params=_one_unit_net(8, -1.0))
+    gm.install()
+    with nb.Plan(1, N, eps, use_picker=True) as p:
+        p.setpts(*pts)
+        assert p.tiles()["method"] == 1
+        assert _rel(p.execute(c=c).cpu().numpy(), ref.cpu().numpy()) < 1e-5
+    # destroying the installed picker uninstalls it
+    gm.close()
+    with nb.Plan(1, N, eps, use_picker=True) as p:
+        p.setpts(*pts)
+        assert p.tiles()["method"] == 3 and p.tiles()["bin"] == (16, 16, 1)
+    big.close()
+
+
+PICKED = [
+    # type, N, M, eps, prec, kind
+    (1, (60, 50), 30000, 1e-3, 0, "mixture"),
+    (2, (40, 36, 30), 20000, 1e-5, 0, "gauss"),
+    (1, (24, 20, 28), 15000, 1e-8, 1, "rand"),
+    (2, (70, 64), 25000, 1e-10, 1, "rand"),
+    (1, (30, 26, 22), 40000, 1e-6, 0, "mixture"),
+]
+
+
+def test_committed_picker_choices_are_accurate(nb):
+    """Whatever tiling the shipped picker chooses, the transform meets the
+    accuracy bar against the exact sums (max(2 eps, the oracle pipeline's own
+    error at the same width + rounding))."""
+    import oracle
+    from paper_2102_08463_gb300 import picker
+    nb.tune_cache_clear()
+    pk = nb.Picker(path=picker.DEFAULT_WEIGHTS)
+    pk.install()
+    try:
+        for i, (tp, N, M, eps, prec, kind) in enumerate(PICKED):
+            dim = len(N)
+            dt = np.float32 if prec == 0 else np.float64
+            ct = np.complex64 if prec == 0 else np.complex128
+            pts = wl.points(kind, dim, M, 900 + i, dt, spread=0.3)
+            p64 = [a.astype(np.float64) for a in pts]
+            with nb.Plan(tp, N, eps, prec=prec, use_picker=True) as p:
+                p.setpts(*[torch.from_numpy(a).cuda() for a in pts])
+                if tp == 1:
+                    c = wl.strengths(M, 950 + i, ct)
+                    got = p.execute(c=torch.from_numpy(c).cuda()).cpu().numpy()
+                    exact = oracle.direct_type1(p64, c.astype(np.complex128), N, +1)
+                    e_or = oracle.rel_l2(oracle.nufft_type1(p64, c.astype(np.complex128), N,
+                                                            eps=eps), exact)
+                else:
+                    f = wl.modes(N, 960 + i, ct)
+                    got = p.execute(f=torch.from_numpy(f).cuda()).cpu().numpy()
+                    exact = oracle.direct_type2(p64, f.astype(np.complex128), +1)
+                    e_or = oracle.rel_l2(oracle.nufft_type2(p64, f.astype(np.complex128),
+                                                            eps=eps), exact)
+                bar = max(2 * eps, e_or + (5 * 2e-5 if prec == 0 else 1e-11))
+                assert oracle.rel_l2(got, exact) <= bar, (tp, N, M, eps, p.tiles())
+    finally:
+        nb.Picker.uninstall()
+        pk.close()
