@@ -127,15 +127,17 @@ __device__ __forceinline__ int wrap_index(int l, int n)
     return l < 0 ? l + n : (l >= n ? l - n : l);
 }
 
-// Atomic complex add into global memory.
+// Atomic complex add into global memory as reductions (no value returned, so
+// the issuing warp does not wait for the L2 round trip): one 8-byte vector
+// reduction for single precision (sm_90+), two 8-byte ones for double.
 __device__ __forceinline__ void atomic_add_cplx(float2 *p, float re, float im)
 {
-    atomicAdd(p, make_float2(re, im));           // vector atomic, sm_90+
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(re), "f"(im) : "memory");
 }
 __device__ __forceinline__ void atomic_add_cplx(double2 *p, double re, double im)
 {
-    atomicAdd(&p->x, re);
-    atomicAdd(&p->y, im);
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->x), "d"(re) : "memory");
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->y), "d"(im) : "memory");
 }
 
 // ---------------------------------------------------------------------------

@@ -721,7 +721,8 @@ int nufft_picker_features(int type, int dim, const int64_t *nmodes, double eps, 
         if (want < 2 * w) want = 2 * w;
         const int64_t nf = next235(want);
         nftot *= (double)nf;
-        const int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
+        int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
+        if (dim == 2 && d == 0 && type == 1 && prec == 0 && w < 16) mdef = 16 - w;   // as makeplan
         int m = tiles->bin[d] > 0 ? tiles->bin[d] : mdef;
         if (m > nf) m = (int)nf;
         t.bin[d] = m;

@@ -289,7 +289,10 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
             int64_t want = (int64_t)ceil(sigma * (double)p.N[d] - 1e-9);
             if (want < 2 * w) want = 2 * w;
             p.nf[d] = next235(want);
+            // 2D single-precision type 1: m0 = 16 - w puts the padded bin in 16
+            // lanes, so the row-sweep spreader runs two points per warp step
             int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
+            if (dim == 2 && d == 0 && type == 1 && prec == 0 && w < 16) mdef = 16 - w;
             int m = o.bin[d] > 0 ? o.bin[d] : mdef;
             if (m > p.nf[d]) m = (int)p.nf[d];
             if (padded(m, w) > 1023) { delete h; return NUFFT_ERR_ARG; }

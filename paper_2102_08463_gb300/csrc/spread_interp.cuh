@@ -235,6 +235,501 @@ spread_sm_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restr
 }
 
 // ---------------------------------------------------------------------------
+// Row-sweep SM spreading, 2D (Sec. 4.1 SM with the accumulation moved from
+// shared-memory atomics into registers).  One warp per work item, cut into
+// S = 32 / L sub-warps of L lanes; lane q of every sub-warp owns column q of the
+// padded bin (p0 = m0 + W <= L) and holds, in registers, the W rows that a
+// window starting at the current row can reach.
+//
+//  1. The subproblem's points are ordered by the first row of their window
+//     (stable counting sort in shared memory: warp-aggregated integer atomics).
+//  2. 32 points at a time, lane i evaluates point i's 2W kernel values and
+//     stores w_y and c w_x in a staging slot.
+//  3. The warp walks the staged points one start row at a time.  Before row r
+//     is entered, every row above r is complete: the sub-warps' copies of it are
+//     summed by shuffles, added to the fine grid (periodic wrap), and the
+//     register window shifts down one row.  The points starting at row r are
+//     dealt to the sub-warps in turn; every lane adds (c w_x[q - s_x]) w_y[k] to
+//     its W rows -- a plain register update, since within a sub-warp no two
+//     lanes own the same cell.
+//  4. The rows still held at the end are added to the fine grid.
+//
+// Shared memory per warp (sweep_bytes): order[msub] and keys[msub] (uint16), the
+// row cursors (m1 + 2 ints) and 32 staging slots.
+// ---------------------------------------------------------------------------
+// Staging slots are built from 16-byte quads (4 floats or 2 doubles): each
+// weight row takes QW = ceil(W / VEC) quads, the key word one more, and the
+// quad count is made odd so that the 8 lanes of a quarter-warp storing their
+// slots with 128-bit stores hit 8 different bank quads.
+template <typename T> __host__ __device__ constexpr int quad_vec() { return 16 / (int)sizeof(T); }
+template <typename T, int W> __host__ __device__ constexpr int quad_row()
+{
+    return (W + quad_vec<T>() - 1) / quad_vec<T>();
+}
+template <typename T, int W, int ROWS> __host__ __device__ constexpr int sweep_slot_t()
+{
+    return (((ROWS * quad_row<T, W>() + 1) | 1) * quad_vec<T>());
+}
+template <typename T, int W>
+__host__ __device__ constexpr int sweep_slot() { return sweep_slot_t<T, W, 3>(); }
+
+// Stores a W-value row as quad_row<T, W>() 16-byte quads, zero-padded.
+template <int W>
+__device__ __forceinline__ void store_row(float *dst, const float (&v)[W])
+{
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+        float4 t;
+        t.x = v[k];
+        t.y = k + 1 < W ? v[k + 1 < W ? k + 1 : k] : 0.f;
+        t.z = k + 2 < W ? v[k + 2 < W ? k + 2 : k] : 0.f;
+        t.w = k + 3 < W ? v[k + 3 < W ? k + 3 : k] : 0.f;
+        *reinterpret_cast<float4 *>(dst + k) = t;
+    }
+}
+template <int W>
+__device__ __forceinline__ void store_row(double *dst, const double (&v)[W])
+{
+#pragma unroll
+    for (int k = 0; k < W; k += 2) {
+        double2 t;
+        t.x = v[k];
+        t.y = k + 1 < W ? v[k + 1 < W ? k + 1 : k] : 0.0;
+        *reinterpret_cast<double2 *>(dst + k) = t;
+    }
+}
+
+// Byte offsets inside a warp's shared memory: order[msub] and keys[msub]
+// (uint16) at 0, the row cursors at sweep_cur, the staging slots at sweep_head
+// (16-byte aligned).
+__host__ __device__ inline size_t sweep_cur(int msub) { return (size_t)4 * msub; }
+__host__ __device__ inline size_t sweep_head(int msub, int m1)
+{
+    return (sweep_cur(msub) + (size_t)4 * (m1 + 2) + 15) & ~(size_t)15;
+}
+
+template <typename T, int W>
+__host__ __device__ inline size_t sweep_bytes(int msub, int m1)
+{
+    return sweep_head(msub, m1) + sizeof(T) * (size_t)32 * sweep_slot<T, W>();
+}
+
+// Single-precision ES kernel for the staging step, written without the
+// cancellation of sqrt(1 - z^2) - 1 near z = 0:
+//   beta (sqrt(1 - z^2) - 1) = -beta z^2 / (1 + sqrt(1 - z^2)),
+// so the hardware reciprocal square root, reciprocal and fast exponential
+// (each ~1e-7 relative) give phi to ~1e-7 relative everywhere.  Double keeps
+// the correctly rounded es_kernel.
+__device__ __forceinline__ float es_kernel_stage(float z, float beta)
+{
+    const float z2 = z * z;
+    const float s = 1.0f - z2;
+    const float r = s > 0.0f ? s * rsqrtf(s) : 0.0f;
+    return s >= 0.0f ? __expf(__fdividef(-beta * z2, 1.0f + r)) : 0.0f;
+}
+__device__ __forceinline__ double es_kernel_stage(double z, double beta)
+{
+    return es_kernel(z, beta);
+}
+
+// A W-value row stored by store_row: whole 16-byte quads (the padding is read
+// and dropped).
+template <int W>
+__device__ __forceinline__ void load_row(const float *s, float (&v)[W])
+{
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(s + k);
+        v[k] = t.x;
+        if (k + 1 < W) v[k + 1 < W ? k + 1 : k] = t.y;
+        if (k + 2 < W) v[k + 2 < W ? k + 2 : k] = t.z;
+        if (k + 3 < W) v[k + 3 < W ? k + 3 : k] = t.w;
+    }
+}
+template <int W>
+__device__ __forceinline__ void load_row(const double *s, double (&v)[W])
+{
+#pragma unroll
+    for (int k = 0; k < W; k += 2) {
+        const double2 t = *reinterpret_cast<const double2 *>(s + k);
+        v[k] = t.x;
+        if (k + 1 < W) v[k + 1 < W ? k + 1 : k] = t.y;
+    }
+}
+
+// Stable counting sort of a subproblem's n points by the first row of their
+// window: the row fields of the points' packed words are gathered through t
+// (eight loads in flight per lane) into keys[], then counted and ranked with
+// warp-aggregated integer atomics.  order[] receives the point indices grouped
+// by row, increasing index within a row.  One warp; cur[] holds nrow + 1
+// cursors.
+template <typename T>
+__device__ __forceinline__ void sweep_row_sort(const typename rec4<T>::type *recs,
+                                               const int32_t *perm, int n, int nrow,
+                                               uint16_t *order, uint16_t *keys, int *cur)
+{
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = lane; i <= nrow; i += 32) cur[i] = 0;
+    for (int base = 0; base < n; base += 32 * U) {
+        uint32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = base + u * 32 + lane;
+            w[u] = k < n ? unpack_word<T>(recs[perm[k]].w) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = base + u * 32 + lane;
+            if (k < n) keys[k] = (uint16_t)((w[u] >> 10) & 1023u);
+        }
+    }
+    __syncwarp();
+    for (int base = 0; base < n; base += 32) {
+        const int k = base + lane;
+        const int key = k < n ? (int)keys[k] : 0x7fffffff;
+        const unsigned peers = __match_any_sync(kFullMask, key);
+        if (k < n && (peers & lt) == 0) atomicAdd(&cur[key + 1], __popc(peers));
+    }
+    __syncwarp();
+    int running = 0;
+    for (int i0 = 1; i0 <= nrow; i0 += 32) {
+        const int i = i0 + lane;
+        int v = i <= nrow ? cur[i] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFullMask, v, o);
+            if (lane >= o) v += t;
+        }
+        if (i <= nrow) cur[i] = running + v;
+        running += __shfl_sync(kFullMask, v, 31);
+    }
+    __syncwarp();
+    for (int base = 0; base < n; base += 32) {
+        const int k = base + lane;
+        const int key = k < n ? (int)keys[k] : 0x7fffffff;
+        const unsigned peers = __match_any_sync(kFullMask, key);
+        const int leader = __ffs(peers) - 1;
+        int pos = 0;
+        if (k < n && lane == leader) pos = atomicAdd(&cur[key], __popc(peers));
+        pos = __shfl_sync(kFullMask, pos, leader);
+        if (k < n) order[pos + __popc(peers & lt)] = (uint16_t)k;
+    }
+    __syncwarp();
+}
+
+template <typename T, int W, int L>
+__device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, int tr,
+                                                   unsigned char *sm, int msub)
+{
+    using C = typename cplx<T>::type;
+    using R = typename rec4<T>::type;
+    constexpr int S = 32 / L;
+    constexpr int SLOT = sweep_slot<T, W>();
+    constexpr int RW = quad_row<T, W>() * quad_vec<T>();   // row stride inside a slot
+    constexpr int OWY = 0, OWR = RW, OWI = 2 * RW, OKEY = 3 * RW;
+    const int lane = threadIdx.x & 31, h = lane / L, q = lane % L;
+    const int4 sub = a.subprob[sp];
+    const int n = sub.z;
+    uint16_t *order = reinterpret_cast<uint16_t *>(sm);
+    uint16_t *keys = order + msub;
+    int *cur = reinterpret_cast<int *>(sm + sweep_cur(msub));
+    T *stg = reinterpret_cast<T *>(sm + sweep_head(msub, a.m1));
+    const int nrow = a.m1 + 1;                            // window start rows 0 .. m1
+    const int32_t *perm = a.perm + sub.y;
+
+    // 1. stable counting sort of the points by window start row
+    sweep_row_sort<T>(a.recs, perm, n, nrow, order, keys, cur);
+
+    // 2.-4. stage and sweep; the next batch's gathers are issued before the
+    // current batch is swept
+    int o0, o1, o2;
+    bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
+    const int P = pad_lo(W);
+    const C *cin = a.cin + (int64_t)tr * a.M;
+    C *grid = a.grid + (int64_t)tr * a.nftot;
+    const bool writer = h == 0 && q < a.p0;
+    const int gx = wrap_any(o0 - P + (q < a.p0 ? q : 0), a.n0);
+    const int row0 = o1 - P;
+    T accr[W], acci[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) accr[r] = acci[r] = (T)0;
+    int row = 0;                                          // padded row held in acc[0]
+
+    auto flush_row = [&](int r_rel, T vr, T vi) {
+#pragma unroll
+        for (int o = L; o < 32; o <<= 1) {
+            vr += __shfl_xor_sync(kFullMask, vr, o);
+            vi += __shfl_xor_sync(kFullMask, vi, o);
+        }
+        if (writer && (vr != (T)0 || vi != (T)0))
+            atomic_add_cplx(&grid[(int64_t)wrap_any(row0 + r_rel, a.n1) * a.n0 + gx], vr, vi);
+    };
+
+    R rc;
+    C cv;
+    auto fetch = [&](int base) {
+        if (base + lane < n) {
+            const int j = perm[order[base + lane]];
+            rc = a.recs[j];
+            cv = cin[j];
+        }
+    };
+    fetch(0);
+    for (int base = 0; base < n; base += 32) {
+        const int cnt = min(32, n - base);
+        int myrow = 0x7fffffff;
+        if (lane < cnt) {
+            const uint32_t pk = unpack_word<T>(rc.w);
+            T *s = stg + lane * SLOT;
+            myrow = (int)((pk >> 10) & 1023u);
+            reinterpret_cast<uint32_t *>(s + OKEY)[0] = pk & 1023u;
+            T vr[W], vi[W], vy[W];
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const T wx = es_kernel_stage(((T)i - rc.x) * a.hw, a.beta);
+                vr[i] = cv.x * wx;
+                vi[i] = cv.y * wx;
+                vy[i] = es_kernel_stage(((T)i - rc.y) * a.hw, a.beta);
+            }
+            store_row<W>(s + OWY, vy);
+            store_row<W>(s + OWR, vr);
+            store_row<W>(s + OWI, vi);
+        }
+        fetch(base + 32);
+        __syncwarp();
+        int i0 = 0;
+        while (i0 < cnt) {
+            const int r = __shfl_sync(kFullMask, myrow, i0);
+            while (row < r) {
+                flush_row(row, accr[0], acci[0]);
+#pragma unroll
+                for (int k = 0; k + 1 < W; ++k) {
+                    accr[k] = accr[k + 1];
+                    acci[k] = acci[k + 1];
+                }
+                accr[W - 1] = acci[W - 1] = (T)0;
+                ++row;
+            }
+            const unsigned later = __ballot_sync(kFullMask, myrow > r) & ~((2u << i0) - 1u);
+            const int i1 = later ? __ffs(later) - 1 : cnt;
+            for (int i = i0 + h; i < i1; i += S) {
+                const T *s = stg + i * SLOT;
+                const int d = q - (int)reinterpret_cast<const uint32_t *>(s + OKEY)[0];
+                const bool in = (unsigned)d < (unsigned)W;
+                const int dd = in ? d : 0;
+                const T wr = in ? s[OWR + dd] : (T)0;
+                const T wi = in ? s[OWI + dd] : (T)0;
+                T wy[W];
+                load_row<W>(s + OWY, wy);
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    accr[k] += wr * wy[k];
+                    acci[k] += wi * wy[k];
+                }
+            }
+            i0 = i1;
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < W; ++r) flush_row(row + r, accr[r], acci[r]);
+}
+
+// ---------------------------------------------------------------------------
+// Row-sweep SM spreading, 3D (single precision, W <= 8, bins m2 = M2 in {1, 2}).
+// As the 2D sweep with S = 1: lane q owns x column q of the padded bin, and
+// holds the W y rows in reach times all M2 + W z planes of the padded bin in
+// registers.  One point per warp step, so its window's first plane s_z is
+// warp-uniform and selects one of M2 + 1 unrolled updates
+//   acc[j][s_z + k] += (c w_x[q - s_x] w_y[j]) w_z[k],  j, k < W.
+// A finished row is added to the fine grid plane by plane.
+// ---------------------------------------------------------------------------
+template <typename T, int W>
+__host__ __device__ inline size_t sweep3_bytes(int msub, int m1)
+{
+    return sweep_head(msub, m1) + sizeof(T) * (size_t)32 * sweep_slot_t<T, W, 4>();
+}
+
+template <typename T, int W, int PZ, int O>
+__device__ __forceinline__ void sweep3_add(T (&ar)[W][PZ], T (&ai)[W][PZ], const T (&t)[W],
+                                           const T (&u)[W], const T (&wz)[W])
+{
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            ar[j][O + k] += t[j] * wz[k];
+            ai[j][O + k] += u[j] * wz[k];
+        }
+    }
+}
+
+template <typename T, int W, int M2>
+__device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, int tr,
+                                                   unsigned char *sm, int msub)
+{
+    using C = typename cplx<T>::type;
+    using R = typename rec4<T>::type;
+    constexpr int PZ = M2 + W;
+    constexpr int SLOT = sweep_slot_t<T, W, 4>();
+    constexpr int RW = quad_row<T, W>() * quad_vec<T>();
+    constexpr int OWY = 0, OWZ = RW, OWR = 2 * RW, OWI = 3 * RW, OKEY = 4 * RW;
+    const int lane = threadIdx.x & 31;
+    const int4 sub = a.subprob[sp];
+    const int n = sub.z;
+    uint16_t *order = reinterpret_cast<uint16_t *>(sm);
+    uint16_t *keys = order + msub;
+    int *cur = reinterpret_cast<int *>(sm + sweep_cur(msub));
+    T *stg = reinterpret_cast<T *>(sm + sweep_head(msub, a.m1));
+    const int nrow = a.m1 + 1;
+    const int32_t *perm = a.perm + sub.y;
+
+    sweep_row_sort<T>(a.recs, perm, n, nrow, order, keys, cur);
+
+    int o0, o1, o2;
+    bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
+    const int P = pad_lo(W);
+    const C *cin = a.cin + (int64_t)tr * a.M;
+    C *grid = a.grid + (int64_t)tr * a.nftot;
+    const bool writer = lane < a.p0;
+    const int gx = wrap_any(o0 - P + (writer ? lane : 0), a.n0);
+    const int row0 = o1 - P, plane0 = o2 - P;
+    T accr[W][PZ], acci[W][PZ];
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+#pragma unroll
+        for (int k = 0; k < PZ; ++k) accr[j][k] = acci[j][k] = (T)0;
+    int row = 0;
+
+    auto flush_row = [&](int r_rel, const T (&vr)[PZ], const T (&vi)[PZ]) {
+        if (!writer) return;
+        const int gy = wrap_any(row0 + r_rel, a.n1);
+#pragma unroll
+        for (int k = 0; k < PZ; ++k) {
+            if (vr[k] != (T)0 || vi[k] != (T)0) {
+                const int gz = wrap_any(plane0 + k, a.n2);
+                atomic_add_cplx(&grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx], vr[k], vi[k]);
+            }
+        }
+    };
+
+    R rc;
+    C cv;
+    auto fetch = [&](int base) {
+        if (base + lane < n) {
+            const int j = perm[order[base + lane]];
+            rc = a.recs[j];
+            cv = cin[j];
+        }
+    };
+    fetch(0);
+    for (int base = 0; base < n; base += 32) {
+        const int cnt = min(32, n - base);
+        int myrow = 0x7fffffff;
+        if (lane < cnt) {
+            const uint32_t pk = unpack_word<T>(rc.w);
+            T *s = stg + lane * SLOT;
+            myrow = (int)((pk >> 10) & 1023u);
+            reinterpret_cast<uint32_t *>(s + OKEY)[0] = (pk & 1023u) | ((pk >> 20) << 16);
+            T vr[W], vi[W], vy[W], vz[W];
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const T wx = es_kernel_stage(((T)i - rc.x) * a.hw, a.beta);
+                vr[i] = cv.x * wx;
+                vi[i] = cv.y * wx;
+                vy[i] = es_kernel_stage(((T)i - rc.y) * a.hw, a.beta);
+                vz[i] = es_kernel_stage(((T)i - rc.z) * a.hw, a.beta);
+            }
+            store_row<W>(s + OWY, vy);
+            store_row<W>(s + OWZ, vz);
+            store_row<W>(s + OWR, vr);
+            store_row<W>(s + OWI, vi);
+        }
+        fetch(base + 32);
+        __syncwarp();
+        int i0 = 0;
+        while (i0 < cnt) {
+            const int r = __shfl_sync(kFullMask, myrow, i0);
+            while (row < r) {
+                flush_row(row, accr[0], acci[0]);
+#pragma unroll
+                for (int j = 0; j + 1 < W; ++j)
+#pragma unroll
+                    for (int k = 0; k < PZ; ++k) {
+                        accr[j][k] = accr[j + 1][k];
+                        acci[j][k] = acci[j + 1][k];
+                    }
+#pragma unroll
+                for (int k = 0; k < PZ; ++k) accr[W - 1][k] = acci[W - 1][k] = (T)0;
+                ++row;
+            }
+            const unsigned later = __ballot_sync(kFullMask, myrow > r) & ~((2u << i0) - 1u);
+            const int i1 = later ? __ffs(later) - 1 : cnt;
+            for (int i = i0; i < i1; ++i) {
+                const T *s = stg + i * SLOT;
+                const uint32_t kw = reinterpret_cast<const uint32_t *>(s + OKEY)[0];
+                const int d = lane - (int)(kw & 0xffffu);
+                const int sz = (int)(kw >> 16);
+                const bool in = (unsigned)d < (unsigned)W;
+                const int dd = in ? d : 0;
+                const T wr = in ? s[OWR + dd] : (T)0;
+                const T wi = in ? s[OWI + dd] : (T)0;
+                T wy[W], wz[W], t[W], u[W];
+                load_row<W>(s + OWY, wy);
+                load_row<W>(s + OWZ, wz);
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    t[j] = wr * wy[j];
+                    u[j] = wi * wy[j];
+                }
+                if (sz == 0)
+                    sweep3_add<T, W, PZ, 0>(accr, acci, t, u, wz);
+                else if (M2 == 1 || sz == 1)
+                    sweep3_add<T, W, PZ, 1>(accr, acci, t, u, wz);
+                else
+                    sweep3_add<T, W, PZ, (M2 >= 2 ? 2 : 1)>(accr, acci, t, u, wz);
+            }
+            i0 = i1;
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) flush_row(row + j, accr[j], acci[j]);
+}
+
+template <typename T, int W, int M2>
+__global__ void __launch_bounds__(128)
+spread_sweep3_kernel(KArgs<T> a, int msub, int warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char *sm = smem_raw + (size_t)warp * warp_bytes;
+    const int per_cta = blockDim.x >> 5;
+    const int nsp = *a.nsub;
+    const int64_t nwork = (int64_t)nsp * a.ntransf;
+    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
+         wi += (int64_t)gridDim.x * per_cta)
+        spread_sweep3_item<T, W, M2>(a, (int)(wi % nsp), (int)(wi / nsp), sm, msub);
+}
+
+template <typename T, int W, int L>
+__global__ void __launch_bounds__(256)
+spread_sweep2_kernel(KArgs<T> a, int msub, int warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char *sm = smem_raw + (size_t)warp * warp_bytes;
+    const int per_cta = blockDim.x >> 5;
+    const int nsp = *a.nsub;
+    const int64_t nwork = (int64_t)nsp * a.ntransf;
+    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
+         wi += (int64_t)gridDim.x * per_cta)
+        spread_sweep2_item<T, W, L>(a, (int)(wi % nsp), (int)(wi / nsp), sm, msub);
+}
+
+// ---------------------------------------------------------------------------
 // GM-sort spreading: bin-ordered points, global atomics.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int W>
@@ -521,6 +1016,182 @@ __device__ __forceinline__ void interp_sorted_item(const KArgs<T> &a, int sp, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Sorted interpolation with one thread per point (Sec. 4.2).  The CTA stages
+// the subproblem's padded bin in shared memory (STAGED; coalesced row loads
+// with periodic wrap) or reads the fine grid directly (GM-sort), then every
+// thread takes points of the subproblem: it evaluates its point's d W kernel
+// values and accumulates the W^d window as sum_z w_z sum_y w_y sum_x w_x g --
+// no shuffles and no cross-lane sums, every lane busy with its own point.
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int W, bool STAGED>
+__device__ __forceinline__ void interp_lane_item(const KArgs<T> &a, int sp, int tr,
+                                                 typename cplx<T>::type *tile)
+{
+    using C = typename cplx<T>::type;
+    using R = typename rec4<T>::type;
+    const int P = pad_lo(W);
+    const int4 sub = a.subprob[sp];
+    int o0, o1, o2;
+    bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
+    const C *grid = a.grid + (int64_t)tr * a.nftot;
+    C *cout = a.cout + (int64_t)tr * a.M;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    if (STAGED) {
+        const int rows = a.p1 * (DIM == 3 ? a.p2 : 1);
+        for (int rr = warp; rr < rows; rr += nwarps) {
+            const int ry = rr % a.p1, rz = rr / a.p1;
+            const int gy = wrap_any(o1 - P + ry, a.n1);
+            const int gz = DIM == 3 ? wrap_any(o2 - P + rz, a.n2) : 0;
+            const C *src = grid + ((int64_t)gz * a.n1 + gy) * a.n0;
+            for (int rx = lane; rx < a.p0; rx += 32)
+                tile[rr * a.p0 + rx] = src[wrap_any(o0 - P + rx, a.n0)];
+        }
+        __syncthreads();
+    }
+    const int32_t *perm = a.perm + sub.y;
+    for (int k = threadIdx.x; k < sub.z; k += blockDim.x) {
+        const int j = perm[k];
+        const R rc = a.recs[j];
+        const uint32_t pk = unpack_word<T>(rc.w);
+        const int sx = pk & 1023u, sy = (pk >> 10) & 1023u, sz = pk >> 20;
+        T wx[W], wy[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            wx[i] = es_kernel_stage(((T)i - rc.x) * a.hw, a.beta);
+            wy[i] = es_kernel_stage(((T)i - rc.y) * a.hw, a.beta);
+        }
+        int gxs[STAGED ? 1 : W];
+        if (!STAGED) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) gxs[STAGED ? 0 : i] = wrap_any(o0 - P + sx + i, a.n0);
+        }
+        T ar = 0, ai = 0;
+        const int nz = DIM == 3 ? W : 1;
+#pragma unroll 1
+        for (int iz = 0; iz < nz; ++iz) {
+            T zr = 0, zi = 0;
+            const int gz = DIM == 3 && !STAGED ? wrap_any(o2 - P + sz + iz, a.n2) : 0;
+#pragma unroll
+            for (int iy = 0; iy < W; ++iy) {
+                T yr = 0, yi = 0;
+                if (STAGED) {
+                    const C *t = tile + ((sz + iz) * a.p1 + sy + iy) * a.p0 + sx;
+#pragma unroll
+                    for (int ix = 0; ix < W; ++ix) {
+                        const C g = t[ix];
+                        yr += wx[ix] * g.x;
+                        yi += wx[ix] * g.y;
+                    }
+                } else {
+                    const int gy = wrap_any(o1 - P + sy + iy, a.n1);
+                    const C *row = grid + ((int64_t)gz * a.n1 + gy) * a.n0;
+#pragma unroll
+                    for (int ix = 0; ix < W; ++ix) {
+                        const C g = row[gxs[STAGED ? 0 : ix]];
+                        yr += wx[ix] * g.x;
+                        yi += wx[ix] * g.y;
+                    }
+                }
+                zr += wy[iy] * yr;
+                zi += wy[iy] * yi;
+            }
+            const T vz = DIM == 3 ? es_kernel_stage(((T)iz - rc.z) * a.hw, a.beta) : (T)1;
+            ar += vz * zr;
+            ai += vz * zi;
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        cout[j] = o;
+    }
+    if (STAGED) __syncthreads();
+}
+
+// 2D, one warp per work item: the warp stages its own padded bin (no CTA
+// barriers, so many subproblems are in flight per SM) and its lanes take the
+// subproblem's points as above.
+template <typename T, int W>
+__device__ __forceinline__ void interp_warp2_item(const KArgs<T> &a, int sp, int tr,
+                                                  typename cplx<T>::type *tile)
+{
+    using C = typename cplx<T>::type;
+    using R = typename rec4<T>::type;
+    const int P = pad_lo(W);
+    const int lane = threadIdx.x & 31;
+    const int4 sub = a.subprob[sp];
+    int o0, o1, o2;
+    bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
+    const C *grid = a.grid + (int64_t)tr * a.nftot;
+    C *cout = a.cout + (int64_t)tr * a.M;
+    const int ptot = a.p0 * a.p1;
+    for (int i = lane; i < ptot; i += 32) {
+        const int ry = i / a.p0, rx = i - ry * a.p0;
+        tile[i] = grid[(int64_t)wrap_any(o1 - P + ry, a.n1) * a.n0 + wrap_any(o0 - P + rx, a.n0)];
+    }
+    __syncwarp();
+    const int32_t *perm = a.perm + sub.y;
+    for (int k = lane; k < sub.z; k += 32) {
+        const int j = perm[k];
+        const R rc = a.recs[j];
+        const uint32_t pk = unpack_word<T>(rc.w);
+        const int sx = pk & 1023u, sy = (pk >> 10) & 1023u;
+        T wx[W], wy[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            wx[i] = es_kernel_stage(((T)i - rc.x) * a.hw, a.beta);
+            wy[i] = es_kernel_stage(((T)i - rc.y) * a.hw, a.beta);
+        }
+        T ar = 0, ai = 0;
+#pragma unroll
+        for (int iy = 0; iy < W; ++iy) {
+            const C *t = tile + (sy + iy) * a.p0 + sx;
+            T yr = 0, yi = 0;
+#pragma unroll
+            for (int ix = 0; ix < W; ++ix) {
+                const C g = t[ix];
+                yr += wx[ix] * g.x;
+                yi += wx[ix] * g.y;
+            }
+            ar += wy[iy] * yr;
+            ai += wy[iy] * yi;
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        cout[j] = o;
+    }
+    __syncwarp();
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256)
+interp_warp2_kernel(KArgs<T> a, int tile_elems)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    auto *tile = reinterpret_cast<typename cplx<T>::type *>(smem_raw) + (size_t)warp * tile_elems;
+    const int per_cta = blockDim.x >> 5;
+    const int nsp = *a.nsub;
+    const int64_t nwork = (int64_t)nsp * a.ntransf;
+    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
+         wi += (int64_t)gridDim.x * per_cta)
+        interp_warp2_item<T, W>(a, (int)(wi % nsp), (int)(wi / nsp), tile);
+}
+
+template <typename T, int DIM, int W, bool STAGED>
+__global__ void __launch_bounds__(256)
+interp_lane_kernel(KArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto *tile = reinterpret_cast<typename cplx<T>::type *>(smem_raw);
+    const int nsp = *a.nsub;
+    const int64_t nwork = (int64_t)nsp * a.ntransf;
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x)
+        interp_lane_item<T, DIM, W, STAGED>(a, (int)(wi % nsp), (int)(wi / nsp), tile);
+}
+
 template <typename T, int DIM, int W, bool STAGED>
 __global__ void __launch_bounds__(256)
 interp_sorted_kernel(KArgs<T> a)
@@ -666,6 +1337,41 @@ inline int persistent_grid(const Plan &p, K kernel, int threads, size_t smem)
     return p.num_sms * per_sm;
 }
 
+// Launches the row-sweep kernel with as many warps per CTA as the shared memory
+// allows (at most threads / 32); returns false, launching nothing, when fewer
+// than two fit.
+template <typename T, int W, int L>
+bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
+{
+    const size_t warp_bytes = sweep_bytes<T, W>(p.msub, a.m1);
+    int nw = threads / 32;
+    while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
+    if (nw < 2) return false;
+    const size_t smem = warp_bytes * nw;
+    auto k = spread_sweep2_kernel<T, W, L>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, p.msub,
+                                                                        (int)warp_bytes);
+    *err = cudaGetLastError();
+    return true;
+}
+
+template <typename T, int W, int M2>
+bool launch_sweep3(Plan &p, const KArgs<T> &a, cudaError_t *err)
+{
+    const size_t warp_bytes = sweep3_bytes<T, W>(p.msub, a.m1);
+    int nw = 4;
+    while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
+    if (nw < 2) return false;
+    const size_t smem = warp_bytes * nw;
+    auto k = spread_sweep3_kernel<T, W, M2>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, p.msub,
+                                                                        (int)warp_bytes);
+    *err = cudaGetLastError();
+    return true;
+}
+
 template <typename T, int DIM, int W>
 cudaError_t spread_w(Plan &p, const void *c)
 {
@@ -673,6 +1379,21 @@ cudaError_t spread_w(Plan &p, const void *c)
     a.cin = reinterpret_cast<const typename cplx<T>::type *>(c);
     const int threads = p.threads;
     count_launch();
+    if constexpr (DIM == 3 && sizeof(T) == 4 && W <= 8) {
+        if (p.method == NUFFT_METHOD_SM && a.p0 <= 32 && p.msub <= 65535 &&
+            (a.m2 == 1 || a.m2 == 2)) {
+            cudaError_t e = cudaSuccess;
+            if (a.m2 == 1 ? launch_sweep3<T, W, 1>(p, a, &e) : launch_sweep3<T, W, 2>(p, a, &e))
+                return e;
+        }
+    }
+    if (p.method == NUFFT_METHOD_SM && DIM == 2 && a.p0 <= 32 && p.msub <= 65535) {
+        cudaError_t e = cudaSuccess;
+        if (a.p0 <= 8 ? launch_sweep2<T, W, 8>(p, a, threads, &e)
+                      : a.p0 <= 16 ? launch_sweep2<T, W, 16>(p, a, threads, &e)
+                                   : launch_sweep2<T, W, 32>(p, a, threads, &e))
+            return e;
+    }
     if (p.method == NUFFT_METHOD_SM) {
         const size_t smem = (size_t)2 * sizeof(T) * a.p0 * a.p1 * a.p2;
         auto k = spread_sm_kernel<T, DIM, W>;
@@ -701,13 +1422,27 @@ cudaError_t interp_w(Plan &p, void *c)
     a.cout = reinterpret_cast<typename cplx<T>::type *>(c);
     const int threads = p.threads;
     count_launch();
+    if (p.method == NUFFT_METHOD_SM && DIM == 2) {
+        // one padded bin per warp, as many warps per CTA as shared memory allows
+        const int tile = a.p0 * a.p1;
+        const size_t per_warp = sizeof(typename cplx<T>::type) * (size_t)tile;
+        int nw = threads / 32;
+        while (nw > 1 && (size_t)nw * per_warp > (size_t)p.smem_optin) --nw;
+        if ((size_t)nw * per_warp <= (size_t)p.smem_optin) {
+            const size_t smem = per_warp * nw;
+            auto k = interp_warp2_kernel<T, W>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, tile);
+            return cudaGetLastError();
+        }
+    }
     if (p.method == NUFFT_METHOD_SM) {
         const size_t smem = sizeof(typename cplx<T>::type) * a.p0 * a.p1 * a.p2;
-        auto k = interp_sorted_kernel<T, DIM, W, true>;
+        auto k = interp_lane_kernel<T, DIM, W, true>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<persistent_grid(p, k, threads, smem), threads, smem, p.stream>>>(a);
     } else if (p.method == NUFFT_METHOD_GM_SORT) {
-        auto k = interp_sorted_kernel<T, DIM, W, false>;
+        auto k = interp_lane_kernel<T, DIM, W, false>;
         k<<<persistent_grid(p, k, threads, 0), threads, 0, p.stream>>>(a);
     } else {
         auto k = interp_gm_kernel<T, DIM, W>;

@@ -66,14 +66,14 @@ def test_algorithmic_cost_per_point_matches_formulas():
 def test_picker_features_without_gpu(lib):
     from paper_2102_08463_gb300 import binding as nb
     # 2D type 1, N = 1024^2, eps 1e-5: w = 6, n = 2048^2; M = n_tot; default tiles (SM,
-    # 16 x 16 bins, M_sub 1024, 256 threads)
+    # (16 - w) x 16 = 10 x 16 bins, M_sub 1024, 256 threads)
+    import math
     f = nb.picker_features(1, (1024, 1024), 1e-5, 2048 * 2048, 1.5, "sm")
-    want = [0, 0, 0, 6 / 16, 22 / 32, 0.0, 1.5 / 16, 1, 0, 8 / 12, 10 / 12, 1.0]
+    want = [0, 0, 0, 6 / 16, 22 / 32, 0.0, 1.5 / 16, 1, 0, math.log2(160) / 12, 10 / 12, 1.0]
     assert f == pytest.approx(want, abs=1e-7)
     # 3D type 2 double, N = 100^3 at eps 1e-9 (w = 10, n = 200^3), GM, 8x8x4 bins
     f = nb.picker_features(2, (100, 100, 100), 1e-9, 1000, 0.0, "gm", bins=(8, 8, 4), msub=256,
                            threads=128)
-    import math
     assert f[:4] == pytest.approx([1, 1, 1, 10 / 16])
     assert f[4] == pytest.approx(math.log2(200 ** 3) / 32, abs=1e-7)
     assert f[5] == pytest.approx(math.log2(1000 / 200 ** 3) / 8, abs=1e-7)

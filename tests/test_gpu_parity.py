@@ -123,6 +123,65 @@ def test_spread_grid_matches_oracle(nb, method, dim, prec, eps):
     p.close()
 
 
+# 2D shared-memory spreading runs as a register row sweep with sub-warps of 8,
+# 16 or 32 lanes (padded bin width m0 + w <= 8 / 16 / 32); each width, tall and
+# short bins, several subproblems per bin (small M_sub), clustered points and
+# ntransf > 1 against the oracle's spread.
+@pytest.mark.parametrize("bins,msub,eps,prec,kind,nt", [
+    ((2, 64), 1024, 1e-5, 0, "rand", 1),       # 8 lanes
+    ((5, 16), 64, 1e-2, 0, "cluster", 1),      # 8 lanes, w = 3
+    ((10, 16), 1024, 1e-5, 0, "rand", 2),      # 16 lanes
+    ((10, 7), 100, 1e-5, 0, "cluster", 1),     # 16 lanes, short bins
+    ((16, 16), 1024, 1e-5, 0, "gauss", 1),     # 32 lanes
+    ((26, 40), 4096, 1e-5, 0, "rand", 1),      # 32 lanes, large M_sub
+    ((6, 16), 256, 1e-9, 1, "rand", 1),        # double, w = 10, 16 lanes
+    ((16, 8), 512, 1e-12, 1, "cluster", 1),    # double, w = 13, 32 lanes
+])
+def test_sweep_spread_matches_oracle(nb, bins, msub, eps, prec, kind, nt):
+    N = (50, 46)
+    M = 7001
+    dt = np.float32 if prec == 0 else np.float64
+    ct = np.complex64 if prec == 0 else np.complex128
+    p = _plan(nb, 1, N, eps, prec, method="sm", bins=bins, msub=msub, ntransf=nt)
+    w, beta, nf = p.params["w"], p.params["beta"], p.params["nf"][:2]
+    pts = wl.points(kind, 2, M, 17 + bins[0], dt, n=nf, spread=0.2)
+    c = wl.strengths(M, 18, ct, ntransf=nt)
+    p.setpts(*_pts_dev(pts, prec))
+    nb.spread(p.handle, nb._dptr(_dev(c)))
+    g = _host(p.finegrid())
+    for t in range(nt):
+        ref = oracle.spread([q.astype(np.float64) for q in pts],
+                            (c[t] if nt > 1 else c).astype(np.complex128), nf, w, beta)
+        assert oracle.rel_l2(g[t] if nt > 1 else g, ref) < _tol(prec)
+    p.close()
+
+
+# 3D single-precision shared-memory spreading runs as a register row sweep for
+# w <= 8 and bins one or two cells deep in z; widths, depths, clustered points
+# and small M_sub against the oracle's spread.
+@pytest.mark.parametrize("bins,msub,eps,kind,nt", [
+    ((16, 16, 2), 1024, 1e-6, "rand", 1),      # w = 7
+    ((16, 8, 1), 128, 1e-5, "cluster", 1),     # w = 6, m2 = 1, many subproblems per bin
+    ((25, 16, 2), 512, 1e-2, "gauss", 2),      # w = 3, widest bins, ntransf 2
+    ((8, 16, 2), 64, 1e-4, "rand", 1),         # w = 5
+])
+def test_sweep3_spread_matches_oracle(nb, bins, msub, eps, kind, nt):
+    N = (26, 22, 20)
+    M = 9001
+    p = _plan(nb, 1, N, eps, 0, method="sm", bins=bins, msub=msub, ntransf=nt)
+    w, beta, nf = p.params["w"], p.params["beta"], p.params["nf"][:3]
+    pts = wl.points(kind, 3, M, 31 + bins[0], np.float32, n=nf, spread=0.3)
+    c = wl.strengths(M, 32, np.complex64, ntransf=nt)
+    p.setpts(*_pts_dev(pts, 0))
+    nb.spread(p.handle, nb._dptr(_dev(c)))
+    g = _host(p.finegrid())
+    for t in range(nt):
+        ref = oracle.spread([q.astype(np.float64) for q in pts],
+                            (c[t] if nt > 1 else c).astype(np.complex128), nf, w, beta)
+        assert oracle.rel_l2(g[t] if nt > 1 else g, ref) < _tol(0)
+    p.close()
+
+
 # ---------------------------------------------------------------------------
 # full transforms, small sizes spanning several bins and a ragged tail
 # ---------------------------------------------------------------------------

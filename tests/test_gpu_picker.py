@@ -162,7 +162,7 @@ def test_plan_takes_the_pickers_argmin(nb):
     # no picker installed: the heuristic tiles stay
     with nb.Plan(1, N, eps, use_picker=True) as p:
         p.setpts(*pts)
-        assert p.tiles() == dict(method=3, bin=(16, 16, 1), msub=1024, threads=256)
+        assert p.tiles() == dict(method=3, bin=(10, 16, 1), msub=1024, threads=256)
         ref = p.execute(c=c)
     # y = -log2(bin cells) / 12: the largest bins win, first in candidate order
     # (SM before GM-sort, M_sub 256 and 128 threads first)
@@ -187,7 +187,7 @@ def test_plan_takes_the_pickers_argmin(nb):
     gm.close()
     with nb.Plan(1, N, eps, use_picker=True) as p:
         p.setpts(*pts)
-        assert p.tiles()["method"] == 3 and p.tiles()["bin"] == (16, 16, 1)
+        assert p.tiles()["method"] == 3 and p.tiles()["bin"] == (10, 16, 1)
     big.close()
 
 
