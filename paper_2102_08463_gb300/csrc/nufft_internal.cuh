@@ -19,6 +19,20 @@ constexpr int kMaxW = 16;
 extern std::atomic<unsigned long long> g_launch_count;
 inline void count_launch(unsigned n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
 constexpr int kDefaultThreads = 256;
+constexpr int kPolyTerms = 17;     // polynomial degree <= 16
+// Default 2D type 1 bins, sized for the row-sweep spreader: the padded width
+// m0 + w fills 8 lanes (w <= 3, single precision) or 16 lanes, so a warp
+// sweeps 4 or 2 points per step; taller bins in double precision and at
+// small w amortise the row flushes.
+inline int default_bin_2d_type1(int axis, int prec, int w)
+{
+    if (prec == 0 && w <= 3) return axis == 0 ? 8 - w : 32;
+    if (axis == 0) return w <= 15 ? 16 - w : 32 - w;
+    return prec == 0 ? 16 : 32;
+}
+// Degree of the kernel polynomials: enough for 2e-8 (single) / 1e-14 (double)
+// on the interior window cells at every width.
+__host__ __device__ constexpr int poly_degree(int prec) { return prec == 0 ? 10 : 16; }
 
 // Complex storage types matching cuFFT's interleaved layout.
 template <typename T> struct cplx;
@@ -190,6 +204,11 @@ struct Plan {
     int smem_optin = 0;            // max dynamic shared memory per CTA (bytes)
     int smem_per_sm = 0;           // shared memory per SM (bytes)
     bool auto_tiles = false;       // method, bins and msub left to the library
+    // Piecewise polynomial form of the kernel: for interior window cell i
+    // (1 <= i <= w - 2), phi((i - delta) 2 / w) = sum_d poly[i][d] s^d with
+    // s = 2 (delta - w/2 + 1) - 1 in (-1, 1]; poly_ok when the fit met its bound.
+    double poly[kMaxW][kPolyTerms] = {};
+    bool poly_ok = false;
     bool use_picker = false;       // consult the installed tile picker at setpts
 };
 
@@ -200,6 +219,10 @@ struct Tiles {
     int msub = 1024;
     int threads = 256;
 };
+// Fits plan.poly (Chebyshev interpolation of each interior cell, converted to
+// monomials in s) and sets plan.poly_ok if the fit is within its bound on a fine
+// sampling of s.
+void fit_kernel_poly(Plan &p);
 // Re-tile an existing plan (keeps its cuFFT plan and fine grid); the points
 // must be set again afterwards.  Returns an NUFFT_ERR_* code.
 int plan_set_tiles(Plan &p, const Tiles &t);

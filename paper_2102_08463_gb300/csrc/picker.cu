@@ -722,7 +722,7 @@ int nufft_picker_features(int type, int dim, const int64_t *nmodes, double eps, 
         const int64_t nf = next235(want);
         nftot *= (double)nf;
         int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
-        if (dim == 2 && d == 0 && type == 1 && prec == 0 && w < 16) mdef = 16 - w;   // as makeplan
+        if (dim == 2 && type == 1) mdef = default_bin_2d_type1(d, prec, w);   // as makeplan
         int m = tiles->bin[d] > 0 ? tiles->bin[d] : mdef;
         if (m > nf) m = (int)nf;
         t.bin[d] = m;

@@ -149,6 +149,63 @@ int default_method(const Plan &p, size_t smem_limit)
 
 }  // namespace
 
+// Interior window cell i of a width-w kernel as a function of s in [-1, 1]:
+// g_i(s) = phi_beta((i + 1 - w/2 - t) 2 / w), t = (s + 1) / 2 (Sec. 3 Eq. (es)).
+static double kernel_cell_value(int w, double beta, int i, double s)
+{
+    const double t = 0.5 * (s + 1.0);
+    const double z = (i + 1 - 0.5 * w - t) * 2.0 / w;
+    const double q = 1.0 - z * z;
+    return q >= 0.0 ? exp(beta * (sqrt(q) - 1.0)) : 0.0;
+}
+
+void nufft::fit_kernel_poly(Plan &p)
+{
+    const int w = p.w, D = poly_degree(p.prec);
+    const double PI = 3.14159265358979323846;
+    for (int i = 0; i < kMaxW; ++i)
+        for (int d = 0; d < kPolyTerms; ++d) p.poly[i][d] = 0.0;
+    double worst = 0.0;
+    for (int i = 1; i + 1 < w; ++i) {
+        // Chebyshev coefficients a_j from the values at the D + 1 first-kind nodes
+        std::vector<double> f(D + 1), a(D + 1);
+        for (int k = 0; k <= D; ++k)
+            f[k] = kernel_cell_value(w, p.beta, i, cos(PI * (k + 0.5) / (D + 1)));
+        for (int j = 0; j <= D; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k <= D; ++k) acc += f[k] * cos(PI * j * (k + 0.5) / (D + 1));
+            a[j] = acc * (j == 0 ? 1.0 : 2.0) / (D + 1);
+        }
+        // sum_j a_j T_j(s) as monomials: T_0 = 1, T_1 = s, T_{j+1} = 2 s T_j - T_{j-1}
+        std::vector<double> tm(D + 1, 0.0), t0(D + 1, 0.0), t1(D + 1, 0.0), c(D + 1, 0.0);
+        t0[0] = 1.0;
+        c[0] += a[0];
+        if (D >= 1) {
+            t1[1] = 1.0;
+            c[1] += a[1];
+        }
+        for (int j = 2; j <= D; ++j) {
+            std::vector<double> tn(D + 1, 0.0);
+            for (int d = 0; d <= D; ++d) {
+                tn[d] = -t0[d];
+                if (d > 0) tn[d] += 2.0 * t1[d - 1];
+            }
+            for (int d = 0; d <= D; ++d) c[d] += a[j] * tn[d];
+            t0 = t1;
+            t1 = tn;
+        }
+        for (int d = 0; d <= D; ++d) p.poly[i][d] = c[d];
+        for (int k = 0; k <= 2000; ++k) {
+            const double s = -1.0 + k / 1000.0;
+            double v = c[D];
+            for (int d = D - 1; d >= 0; --d) v = v * s + c[d];
+            const double e = fabs(v - kernel_cell_value(w, p.beta, i, s));
+            if (e > worst) worst = e;
+        }
+    }
+    p.poly_ok = worst <= (p.prec == 0 ? 3e-8 : 1e-14);
+}
+
 bool nufft::tiles_feasible(const Plan &p, const Tiles &t)
 {
     if (t.method < NUFFT_METHOD_GM || t.method > NUFFT_METHOD_SM) return false;
@@ -268,6 +325,7 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     p.sigma = sigma;
     p.w = w;
     p.beta = kernel_beta(w, sigma);
+    fit_kernel_poly(p);
     p.stream = (cudaStream_t)o.stream;
     p.threads = o.threads ? o.threads : kDefaultThreads;
     p.ctas_per_sm = o.ctas_per_sm;
@@ -289,10 +347,8 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
             int64_t want = (int64_t)ceil(sigma * (double)p.N[d] - 1e-9);
             if (want < 2 * w) want = 2 * w;
             p.nf[d] = next235(want);
-            // 2D single-precision type 1: m0 = 16 - w puts the padded bin in 16
-            // lanes, so the row-sweep spreader runs two points per warp step
             int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
-            if (dim == 2 && d == 0 && type == 1 && prec == 0 && w < 16) mdef = 16 - w;
+            if (dim == 2 && type == 1) mdef = default_bin_2d_type1(d, prec, w);
             int m = o.bin[d] > 0 ? o.bin[d] : mdef;
             if (m > p.nf[d]) m = (int)p.nf[d];
             if (padded(m, w) > 1023) { delete h; return NUFFT_ERR_ARG; }

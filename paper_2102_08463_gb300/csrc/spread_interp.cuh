@@ -47,6 +47,8 @@ struct KArgs {
     int p0, p1, p2;                              // padded bin (m + w)
     T beta;
     T hw;                                        // 2 / w
+    int poly;                                    // use coef for interior cells
+    T coef[kMaxW][kPolyTerms];                   // kernel polynomials (Plan::poly)
 };
 
 template <typename T> __device__ __forceinline__ uint32_t unpack_word(T v);
@@ -227,7 +229,7 @@ spread_sm_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restr
     const int64_t nwork = workoff[nplans];
     for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int pl = batch_plan_of(workoff, nplans, wi);
-        const KArgs<T> a = args[pl];
+        const KArgs<T> &a = args[pl];
         const int64_t local = wi - workoff[pl];
         const int nsp = *a.nsub;
         spread_sm_item<T, DIM, W>(a, (int)(local % nsp), (int)(local / nsp), sre);
@@ -270,8 +272,26 @@ template <typename T, int W, int ROWS> __host__ __device__ constexpr int sweep_s
 {
     return (((ROWS * quad_row<T, W>() + 1) | 1) * quad_vec<T>());
 }
-template <typename T, int W>
-__host__ __device__ constexpr int sweep_slot() { return sweep_slot_t<T, W, 3>(); }
+// 2D slot: w_y row, then c w_x scattered into an L-wide complex row (zeros
+// outside the window), so lane q reads entry q at a fixed address.
+template <typename T, int W, int L> __host__ __device__ constexpr int sweep2_slot()
+{
+    return ((quad_row<T, W>() + 2 * L / quad_vec<T>()) | 1) * quad_vec<T>();
+}
+// 3D slot: w_y, w_z, the L = 32 wide c w_x row, key word.
+template <typename T, int W> __host__ __device__ constexpr int sweep3_slot()
+{
+    return ((2 * quad_row<T, W>() + 64 / quad_vec<T>() + 1) | 1) * quad_vec<T>();
+}
+
+__device__ __forceinline__ void store_zero_quad(float *dst)
+{
+    *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void store_zero_quad(double *dst)
+{
+    *reinterpret_cast<double2 *>(dst) = make_double2(0.0, 0.0);
+}
 
 // Stores a W-value row as quad_row<T, W>() 16-byte quads, zero-padded.
 template <int W>
@@ -299,6 +319,11 @@ __device__ __forceinline__ void store_row(double *dst, const double (&v)[W])
     }
 }
 
+// The row sweeps take a subproblem in pieces of at most kSweepCap points (each
+// piece sorted, swept and flushed on its own), so their shared memory does not
+// grow with M_sub -- the rest of the SM's 256 KB stays L1 cache for the gathers.
+constexpr int kSweepCap = 512;
+
 // Byte offsets inside a warp's shared memory: order[msub] and keys[msub]
 // (uint16) at 0, the row cursors at sweep_cur, the staging slots at sweep_head
 // (16-byte aligned).
@@ -308,10 +333,10 @@ __host__ __device__ inline size_t sweep_head(int msub, int m1)
     return (sweep_cur(msub) + (size_t)4 * (m1 + 2) + 15) & ~(size_t)15;
 }
 
-template <typename T, int W>
+template <typename T, int W, int L>
 __host__ __device__ inline size_t sweep_bytes(int msub, int m1)
 {
-    return sweep_head(msub, m1) + sizeof(T) * (size_t)32 * sweep_slot<T, W>();
+    return sweep_head(msub, m1) + sizeof(T) * (size_t)32 * sweep2_slot<T, W, L>();
 }
 
 // Single-precision ES kernel for the staging step, written without the
@@ -330,6 +355,45 @@ __device__ __forceinline__ float es_kernel_stage(float z, float beta)
 __device__ __forceinline__ double es_kernel_stage(double z, double beta)
 {
     return es_kernel(z, beta);
+}
+
+// The W kernel weights phi((i - delta) 2 / W), i < W, of one axis: interior
+// cells by Horner's rule on the plan's polynomials (constant-bank operands),
+// the two edge cells -- where sqrt(1 - z^2) is not smooth -- directly.
+template <typename T, int W>
+__device__ __forceinline__ void kernel_row(const KArgs<T> &a, T delta, T (&v)[W])
+{
+    constexpr int D = poly_degree(sizeof(T) == 4 ? 0 : 1);
+    if (a.poly) {
+        const T s = (T)2 * (delta - (T)(0.5 * W - 1)) - (T)1;
+#pragma unroll
+        for (int i = 1; i + 1 < W; ++i) {
+            T acc = a.coef[i][D];
+#pragma unroll
+            for (int d = D - 1; d >= 0; --d) acc = acc * s + a.coef[i][d];
+            v[i] = acc;
+        }
+        v[0] = es_kernel_stage(((T)0 - delta) * a.hw, a.beta);
+        v[W - 1] = es_kernel_stage(((T)(W - 1) - delta) * a.hw, a.beta);
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = es_kernel_stage(((T)i - delta) * a.hw, a.beta);
+    }
+}
+
+// One weight phi((i - delta) 2 / W) with a run-time cell index.
+template <typename T, int W>
+__device__ __forceinline__ T kernel_cell(const KArgs<T> &a, T delta, int i)
+{
+    constexpr int D = poly_degree(sizeof(T) == 4 ? 0 : 1);
+    if (a.poly && i > 0 && i < W - 1) {
+        const T s = (T)2 * (delta - (T)(0.5 * W - 1)) - (T)1;
+        T acc = a.coef[i][D];
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) acc = acc * s + a.coef[i][d];
+        return acc;
+    }
+    return es_kernel_stage(((T)i - delta) * a.hw, a.beta);
 }
 
 // A W-value row stored by store_row: whole 16-byte quads (the padding is read
@@ -420,17 +484,16 @@ __device__ __forceinline__ void sweep_row_sort(const typename rec4<T>::type *rec
 }
 
 template <typename T, int W, int L>
-__device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, int tr,
-                                                   unsigned char *sm, int msub)
+__device__ __forceinline__ void spread_sweep2_piece(const KArgs<T> &a, int4 sub, int tr,
+                                                    unsigned char *sm)
 {
+    constexpr int msub = kSweepCap;
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
     constexpr int S = 32 / L;
-    constexpr int SLOT = sweep_slot<T, W>();
-    constexpr int RW = quad_row<T, W>() * quad_vec<T>();   // row stride inside a slot
-    constexpr int OWY = 0, OWR = RW, OWI = 2 * RW, OKEY = 3 * RW;
+    constexpr int SLOT = sweep2_slot<T, W, L>();
+    constexpr int OWY = 0, OCX = quad_row<T, W>() * quad_vec<T>();
     const int lane = threadIdx.x & 31, h = lane / L, q = lane % L;
-    const int4 sub = a.subprob[sp];
     const int n = sub.z;
     uint16_t *order = reinterpret_cast<uint16_t *>(sm);
     uint16_t *keys = order + msub;
@@ -484,18 +547,20 @@ __device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, in
             const uint32_t pk = unpack_word<T>(rc.w);
             T *s = stg + lane * SLOT;
             myrow = (int)((pk >> 10) & 1023u);
-            reinterpret_cast<uint32_t *>(s + OKEY)[0] = pk & 1023u;
-            T vr[W], vi[W], vy[W];
+            const int sx = (int)(pk & 1023u);
+            T vx[W], vy[W];
+            kernel_row<T, W>(a, rc.x, vx);
+            kernel_row<T, W>(a, rc.y, vy);
+#pragma unroll
+            for (int k = 0; k < 2 * L; k += quad_vec<T>()) store_zero_quad(s + OCX + k);
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                const T wx = es_kernel_stage(((T)i - rc.x) * a.hw, a.beta);
-                vr[i] = cv.x * wx;
-                vi[i] = cv.y * wx;
-                vy[i] = es_kernel_stage(((T)i - rc.y) * a.hw, a.beta);
+                C v;
+                v.x = cv.x * vx[i];
+                v.y = cv.y * vx[i];
+                *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) = v;
             }
             store_row<W>(s + OWY, vy);
-            store_row<W>(s + OWR, vr);
-            store_row<W>(s + OWI, vi);
         }
         fetch(base + 32);
         __syncwarp();
@@ -516,17 +581,13 @@ __device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, in
             const int i1 = later ? __ffs(later) - 1 : cnt;
             for (int i = i0 + h; i < i1; i += S) {
                 const T *s = stg + i * SLOT;
-                const int d = q - (int)reinterpret_cast<const uint32_t *>(s + OKEY)[0];
-                const bool in = (unsigned)d < (unsigned)W;
-                const int dd = in ? d : 0;
-                const T wr = in ? s[OWR + dd] : (T)0;
-                const T wi = in ? s[OWI + dd] : (T)0;
+                const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * q);
                 T wy[W];
                 load_row<W>(s + OWY, wy);
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
-                    accr[k] += wr * wy[k];
-                    acci[k] += wi * wy[k];
+                    accr[k] += cx.x * wy[k];
+                    acci[k] += cx.y * wy[k];
                 }
             }
             i0 = i1;
@@ -549,7 +610,7 @@ __device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, in
 template <typename T, int W>
 __host__ __device__ inline size_t sweep3_bytes(int msub, int m1)
 {
-    return sweep_head(msub, m1) + sizeof(T) * (size_t)32 * sweep_slot_t<T, W, 4>();
+    return sweep_head(msub, m1) + sizeof(T) * (size_t)32 * sweep3_slot<T, W>();
 }
 
 template <typename T, int W, int PZ, int O>
@@ -567,17 +628,17 @@ __device__ __forceinline__ void sweep3_add(T (&ar)[W][PZ], T (&ai)[W][PZ], const
 }
 
 template <typename T, int W, int M2>
-__device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, int tr,
-                                                   unsigned char *sm, int msub)
+__device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub, int tr,
+                                                    unsigned char *sm)
 {
+    constexpr int msub = kSweepCap;
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
     constexpr int PZ = M2 + W;
-    constexpr int SLOT = sweep_slot_t<T, W, 4>();
+    constexpr int SLOT = sweep3_slot<T, W>();
     constexpr int RW = quad_row<T, W>() * quad_vec<T>();
-    constexpr int OWY = 0, OWZ = RW, OWR = 2 * RW, OWI = 3 * RW, OKEY = 4 * RW;
+    constexpr int OWY = 0, OWZ = RW, OCX = 2 * RW, OKEY = 2 * RW + 64;
     const int lane = threadIdx.x & 31;
-    const int4 sub = a.subprob[sp];
     const int n = sub.z;
     uint16_t *order = reinterpret_cast<uint16_t *>(sm);
     uint16_t *keys = order + msub;
@@ -632,20 +693,23 @@ __device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, in
             const uint32_t pk = unpack_word<T>(rc.w);
             T *s = stg + lane * SLOT;
             myrow = (int)((pk >> 10) & 1023u);
-            reinterpret_cast<uint32_t *>(s + OKEY)[0] = (pk & 1023u) | ((pk >> 20) << 16);
-            T vr[W], vi[W], vy[W], vz[W];
+            reinterpret_cast<uint32_t *>(s + OKEY)[0] = pk >> 20;
+            const int sx = (int)(pk & 1023u);
+            T vx[W], vy[W], vz[W];
+            kernel_row<T, W>(a, rc.x, vx);
+            kernel_row<T, W>(a, rc.y, vy);
+            kernel_row<T, W>(a, rc.z, vz);
+#pragma unroll
+            for (int k = 0; k < 64; k += quad_vec<T>()) store_zero_quad(s + OCX + k);
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                const T wx = es_kernel_stage(((T)i - rc.x) * a.hw, a.beta);
-                vr[i] = cv.x * wx;
-                vi[i] = cv.y * wx;
-                vy[i] = es_kernel_stage(((T)i - rc.y) * a.hw, a.beta);
-                vz[i] = es_kernel_stage(((T)i - rc.z) * a.hw, a.beta);
+                C v;
+                v.x = cv.x * vx[i];
+                v.y = cv.y * vx[i];
+                *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) = v;
             }
             store_row<W>(s + OWY, vy);
             store_row<W>(s + OWZ, vz);
-            store_row<W>(s + OWR, vr);
-            store_row<W>(s + OWI, vi);
         }
         fetch(base + 32);
         __syncwarp();
@@ -669,13 +733,9 @@ __device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, in
             const int i1 = later ? __ffs(later) - 1 : cnt;
             for (int i = i0; i < i1; ++i) {
                 const T *s = stg + i * SLOT;
-                const uint32_t kw = reinterpret_cast<const uint32_t *>(s + OKEY)[0];
-                const int d = lane - (int)(kw & 0xffffu);
-                const int sz = (int)(kw >> 16);
-                const bool in = (unsigned)d < (unsigned)W;
-                const int dd = in ? d : 0;
-                const T wr = in ? s[OWR + dd] : (T)0;
-                const T wi = in ? s[OWI + dd] : (T)0;
+                const int sz = (int)reinterpret_cast<const uint32_t *>(s + OKEY)[0];
+                const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * lane);
+                const T wr = cx.x, wi = cx.y;
                 T wy[W], wz[W], t[W], u[W];
                 load_row<W>(s + OWY, wy);
                 load_row<W>(s + OWZ, wz);
@@ -699,9 +759,20 @@ __device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, in
     for (int j = 0; j < W; ++j) flush_row(row + j, accr[j], acci[j]);
 }
 
+// A subproblem in pieces of at most kSweepCap points (sub = {bin, start, count}).
+template <typename T, int W, int M2>
+__device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, int tr,
+                                                   unsigned char *sm)
+{
+    const int4 sub = a.subprob[sp];
+    for (int piece = 0; piece < sub.z; piece += kSweepCap)
+        spread_sweep3_piece<T, W, M2>(
+            a, make_int4(sub.x, sub.y + piece, min(kSweepCap, sub.z - piece), 0), tr, sm);
+}
+
 template <typename T, int W, int M2>
 __global__ void __launch_bounds__(128)
-spread_sweep3_kernel(KArgs<T> a, int msub, int warp_bytes)
+spread_sweep3_kernel(KArgs<T> a, int warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
@@ -711,12 +782,22 @@ spread_sweep3_kernel(KArgs<T> a, int msub, int warp_bytes)
     const int64_t nwork = (int64_t)nsp * a.ntransf;
     for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
          wi += (int64_t)gridDim.x * per_cta)
-        spread_sweep3_item<T, W, M2>(a, (int)(wi % nsp), (int)(wi / nsp), sm, msub);
+        spread_sweep3_item<T, W, M2>(a, (int)(wi % nsp), (int)(wi / nsp), sm);
+}
+
+template <typename T, int W, int L>
+__device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, int tr,
+                                                   unsigned char *sm)
+{
+    const int4 sub = a.subprob[sp];
+    for (int piece = 0; piece < sub.z; piece += kSweepCap)
+        spread_sweep2_piece<T, W, L>(
+            a, make_int4(sub.x, sub.y + piece, min(kSweepCap, sub.z - piece), 0), tr, sm);
 }
 
 template <typename T, int W, int L>
 __global__ void __launch_bounds__(256)
-spread_sweep2_kernel(KArgs<T> a, int msub, int warp_bytes)
+spread_sweep2_kernel(KArgs<T> a, int warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
@@ -726,7 +807,7 @@ spread_sweep2_kernel(KArgs<T> a, int msub, int warp_bytes)
     const int64_t nwork = (int64_t)nsp * a.ntransf;
     for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
          wi += (int64_t)gridDim.x * per_cta)
-        spread_sweep2_item<T, W, L>(a, (int)(wi % nsp), (int)(wi / nsp), sm, msub);
+        spread_sweep2_item<T, W, L>(a, (int)(wi % nsp), (int)(wi / nsp), sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -813,7 +894,7 @@ spread_gmsort_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__r
     const int64_t nwork = workoff[nplans];
     for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int pl = batch_plan_of(workoff, nplans, wi);
-        const KArgs<T> a = args[pl];
+        const KArgs<T> &a = args[pl];
         const int64_t local = wi - workoff[pl];
         const int nsp = *a.nsub;
         spread_gmsort_item<T, DIM, W>(a, (int)(local % nsp), (int)(local / nsp));
@@ -1057,11 +1138,8 @@ __device__ __forceinline__ void interp_lane_item(const KArgs<T> &a, int sp, int 
         const uint32_t pk = unpack_word<T>(rc.w);
         const int sx = pk & 1023u, sy = (pk >> 10) & 1023u, sz = pk >> 20;
         T wx[W], wy[W];
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-            wx[i] = es_kernel_stage(((T)i - rc.x) * a.hw, a.beta);
-            wy[i] = es_kernel_stage(((T)i - rc.y) * a.hw, a.beta);
-        }
+        kernel_row<T, W>(a, rc.x, wx);
+        kernel_row<T, W>(a, rc.y, wy);
         int gxs[STAGED ? 1 : W];
         if (!STAGED) {
 #pragma unroll
@@ -1097,7 +1175,7 @@ __device__ __forceinline__ void interp_lane_item(const KArgs<T> &a, int sp, int 
                 zr += wy[iy] * yr;
                 zi += wy[iy] * yi;
             }
-            const T vz = DIM == 3 ? es_kernel_stage(((T)iz - rc.z) * a.hw, a.beta) : (T)1;
+            const T vz = DIM == 3 ? kernel_cell<T, W>(a, rc.z, iz) : (T)1;
             ar += vz * zr;
             ai += vz * zi;
         }
@@ -1138,11 +1216,8 @@ __device__ __forceinline__ void interp_warp2_item(const KArgs<T> &a, int sp, int
         const uint32_t pk = unpack_word<T>(rc.w);
         const int sx = pk & 1023u, sy = (pk >> 10) & 1023u;
         T wx[W], wy[W];
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-            wx[i] = es_kernel_stage(((T)i - rc.x) * a.hw, a.beta);
-            wy[i] = es_kernel_stage(((T)i - rc.y) * a.hw, a.beta);
-        }
+        kernel_row<T, W>(a, rc.x, wx);
+        kernel_row<T, W>(a, rc.y, wy);
         T ar = 0, ai = 0;
 #pragma unroll
         for (int iy = 0; iy < W; ++iy) {
@@ -1214,7 +1289,7 @@ interp_sorted_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__r
     const int64_t nwork = workoff[nplans];
     for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int pl = batch_plan_of(workoff, nplans, wi);
-        const KArgs<T> a = args[pl];
+        const KArgs<T> &a = args[pl];
         const int64_t local = wi - workoff[pl];
         const int nsp = *a.nsub;
         interp_sorted_item<T, DIM, W, STAGED>(a, (int)(local % nsp), (int)(local / nsp), tile);
@@ -1324,6 +1399,9 @@ KArgs<T> make_args(const Plan &p)
     a.p2 = p.dim == 3 ? padded(p.m[2], p.w) : 1;
     a.beta = (T)p.beta;
     a.hw = (T)(2.0 / p.w);
+    a.poly = p.poly_ok ? 1 : 0;
+    for (int i = 0; i < kMaxW; ++i)
+        for (int d = 0; d < kPolyTerms; ++d) a.coef[i][d] = (T)p.poly[i][d];
     return a;
 }
 
@@ -1343,15 +1421,14 @@ inline int persistent_grid(const Plan &p, K kernel, int threads, size_t smem)
 template <typename T, int W, int L>
 bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
 {
-    const size_t warp_bytes = sweep_bytes<T, W>(p.msub, a.m1);
+    const size_t warp_bytes = sweep_bytes<T, W, L>(kSweepCap, a.m1);
     int nw = threads / 32;
     while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
     if (nw < 2) return false;
     const size_t smem = warp_bytes * nw;
     auto k = spread_sweep2_kernel<T, W, L>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, p.msub,
-                                                                        (int)warp_bytes);
+    k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, (int)warp_bytes);
     *err = cudaGetLastError();
     return true;
 }
@@ -1359,15 +1436,14 @@ bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
 template <typename T, int W, int M2>
 bool launch_sweep3(Plan &p, const KArgs<T> &a, cudaError_t *err)
 {
-    const size_t warp_bytes = sweep3_bytes<T, W>(p.msub, a.m1);
+    const size_t warp_bytes = sweep3_bytes<T, W>(kSweepCap, a.m1);
     int nw = 4;
     while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
     if (nw < 2) return false;
     const size_t smem = warp_bytes * nw;
     auto k = spread_sweep3_kernel<T, W, M2>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, p.msub,
-                                                                        (int)warp_bytes);
+    k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, (int)warp_bytes);
     *err = cudaGetLastError();
     return true;
 }
@@ -1380,14 +1456,13 @@ cudaError_t spread_w(Plan &p, const void *c)
     const int threads = p.threads;
     count_launch();
     if constexpr (DIM == 3 && sizeof(T) == 4 && W <= 8) {
-        if (p.method == NUFFT_METHOD_SM && a.p0 <= 32 && p.msub <= 65535 &&
-            (a.m2 == 1 || a.m2 == 2)) {
+        if (p.method == NUFFT_METHOD_SM && a.p0 <= 32 && (a.m2 == 1 || a.m2 == 2)) {
             cudaError_t e = cudaSuccess;
             if (a.m2 == 1 ? launch_sweep3<T, W, 1>(p, a, &e) : launch_sweep3<T, W, 2>(p, a, &e))
                 return e;
         }
     }
-    if (p.method == NUFFT_METHOD_SM && DIM == 2 && a.p0 <= 32 && p.msub <= 65535) {
+    if (p.method == NUFFT_METHOD_SM && DIM == 2 && a.p0 <= 32) {
         cudaError_t e = cudaSuccess;
         if (a.p0 <= 8 ? launch_sweep2<T, W, 8>(p, a, threads, &e)
                       : a.p0 <= 16 ? launch_sweep2<T, W, 16>(p, a, threads, &e)
