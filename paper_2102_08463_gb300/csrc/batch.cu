@@ -34,6 +34,8 @@ __global__ void batch_workoff_kernel(const int32_t *const *__restrict__ nsub,
 
 struct Group {
     int type = 1, dim = 2, prec = 0, w = 0, method = NUFFT_METHOD_SM;
+    int variant = 0;                   // row-sweep form (sweep_variant), part of the key
+    int m1max = 1, tile = 1, smem_optin = 0;
     std::vector<int> members;          // indices into the batch's plans
     size_t smem = 0;                   // max padded-bin bytes over the members
     size_t args_bytes = 0;             // one KArgs<T> per member
@@ -160,6 +162,10 @@ int run_batch(nufft_batch_s *b, void *const *c, void *const *f)
         ml.threads = kDefaultThreads;
         ml.num_sms = b->num_sms;
         ml.smem = g.method == NUFFT_METHOD_SM ? g.smem : 0;
+        ml.smem_optin = (size_t)g.smem_optin;
+        ml.variant = g.variant;
+        ml.m1max = g.m1max;
+        ml.tile = g.tile;
         ml.stream = st;
         e = multi_launch(g, ml);
         if (e != cudaSuccess) return cuda_rc(e);
@@ -212,10 +218,11 @@ int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_
             b->singles.push_back(k);
             continue;
         }
+        const int variant = sweep_variant(p);
         Group *g = nullptr;
         for (Group &cand : b->groups)
             if (cand.type == p.type && cand.dim == p.dim && cand.prec == p.prec && cand.w == p.w &&
-                cand.method == p.method)
+                cand.method == p.method && cand.variant == variant)
                 g = &cand;
         if (!g) {
             b->groups.emplace_back();
@@ -225,11 +232,15 @@ int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_
             g->prec = p.prec;
             g->w = p.w;
             g->method = p.method;
+            g->variant = variant;
+            g->smem_optin = p.smem_optin;
         }
         g->members.push_back(k);
         size_t cells = 1;
         for (int d = 0; d < p.dim; ++d) cells *= (size_t)padded(p.m[d], p.w);
         g->smem = std::max(g->smem, cells * 2 * real_bytes(p.prec));
+        g->tile = std::max(g->tile, (int)cells);
+        g->m1max = std::max(g->m1max, p.m[1]);
     }
     for (Group &g : b->groups) {
         const size_t n = g.members.size();

@@ -279,8 +279,16 @@ struct MultiLaunch {
     int nplans;
     int w, method, threads, num_sms;
     size_t smem;               // shared memory per CTA (max over the plans)
+    size_t smem_optin;         // largest dynamic shared memory per CTA
+    int variant;               // row sweep: 2D lanes (8/16/32), 3D m2 (1/2); 0 = none
+    int m1max;                 // largest bin height over the plans
+    int tile;                  // largest padded bin (cells) over the plans
     cudaStream_t stream;
 };
+// Row-sweep form of a type 1 SM plan (the batch's grouping key): 2D sub-warp
+// lanes 8, 16 or 32; 3D: 1 or 2 (bins one or two cells deep); 0 if the plan uses
+// the shared-memory atomic kernel.
+int sweep_variant(const Plan &p);
 cudaError_t spread_multi_f32_2d(const MultiLaunch &ml);
 cudaError_t spread_multi_f32_3d(const MultiLaunch &ml);
 cudaError_t spread_multi_f64_2d(const MultiLaunch &ml);

@@ -206,6 +206,16 @@ void nufft::fit_kernel_poly(Plan &p)
     p.poly_ok = worst <= (p.prec == 0 ? 3e-8 : 1e-14);
 }
 
+int nufft::sweep_variant(const Plan &p)
+{
+    if (p.type != 1 || p.method != NUFFT_METHOD_SM) return 0;
+    const int p0 = padded(p.m[0], p.w);
+    if (p0 > 32) return 0;
+    if (p.dim == 2) return p0 <= 8 ? 8 : (p0 <= 16 ? 16 : 32);
+    if (p.prec == 0 && p.w <= 8 && (p.m[2] == 1 || p.m[2] == 2)) return p.m[2];
+    return 0;
+}
+
 bool nufft::tiles_feasible(const Plan &p, const Tiles &t)
 {
     if (t.method < NUFFT_METHOD_GM || t.method > NUFFT_METHOD_SM) return false;

@@ -29,7 +29,7 @@ namespace nufft {
 constexpr unsigned kFullMask = 0xffffffffu;
 
 template <typename T>
-struct KArgs {
+struct alignas(16) KArgs {
     const typename rec4<T>::type *recs;
     const int32_t *perm;
     const int4 *subprob;
@@ -1367,6 +1367,139 @@ interp_gm_kernel(KArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
+// Multi-plan (batched) forms of the row sweeps and the one-thread-per-point
+// interpolation.  Work items of all plans of a group are numbered by workoff;
+// a warp (or CTA) copies the KArgs of the plan it is working on into shared
+// memory when the plan changes, so parameter reads -- the kernel polynomial
+// coefficients above all -- are shared-memory broadcasts.  Single-precision
+// groups evaluate the kernel directly (cheaper than coefficients read from
+// shared memory); double precision keeps the polynomials.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void warp_load_args(const KArgs<T> *args, int pl, KArgs<T> *cache,
+                                               int &cached)
+{
+    if (pl == cached) return;
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    const int4 *src = reinterpret_cast<const int4 *>(args + pl);
+    int4 *dst = reinterpret_cast<int4 *>(cache);
+    for (int i = lane; i < (int)(sizeof(KArgs<T>) / 16); i += 32) dst[i] = src[i];
+    __syncwarp();
+    if (sizeof(T) == 4 && lane == 0) cache->poly = 0;
+    __syncwarp();
+    cached = pl;
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t args_slot() { return (sizeof(KArgs<T>) + 15) & ~(size_t)15; }
+
+template <typename T, int W, int L>
+__global__ void __launch_bounds__(256)
+spread_sweep2_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
+                           int nplans, int warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char *base = smem_raw + (size_t)warp * (args_slot<T>() + warp_bytes);
+    KArgs<T> *cache = reinterpret_cast<KArgs<T> *>(base);
+    unsigned char *sm = base + args_slot<T>();
+    const int per_cta = blockDim.x >> 5;
+    int cached = -1;
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
+         wi += (int64_t)gridDim.x * per_cta) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        warp_load_args(args, pl, cache, cached);
+        const KArgs<T> &a = *cache;
+        const int64_t local = wi - workoff[pl];
+        const int nsp = *a.nsub;
+        spread_sweep2_item<T, W, L>(a, (int)(local % nsp), (int)(local / nsp), sm);
+    }
+}
+
+template <typename T, int W, int M2>
+__global__ void __launch_bounds__(128)
+spread_sweep3_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
+                           int nplans, int warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char *base = smem_raw + (size_t)warp * (args_slot<T>() + warp_bytes);
+    KArgs<T> *cache = reinterpret_cast<KArgs<T> *>(base);
+    unsigned char *sm = base + args_slot<T>();
+    const int per_cta = blockDim.x >> 5;
+    int cached = -1;
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
+         wi += (int64_t)gridDim.x * per_cta) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        warp_load_args(args, pl, cache, cached);
+        const KArgs<T> &a = *cache;
+        const int64_t local = wi - workoff[pl];
+        const int nsp = *a.nsub;
+        spread_sweep3_item<T, W, M2>(a, (int)(local % nsp), (int)(local / nsp), sm);
+    }
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256)
+interp_warp2_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
+                          int nplans, int tile_elems)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const size_t slot = args_slot<T>() + sizeof(typename cplx<T>::type) * (size_t)tile_elems;
+    unsigned char *base = smem_raw + (size_t)warp * slot;
+    KArgs<T> *cache = reinterpret_cast<KArgs<T> *>(base);
+    auto *tile = reinterpret_cast<typename cplx<T>::type *>(base + args_slot<T>());
+    const int per_cta = blockDim.x >> 5;
+    int cached = -1;
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
+         wi += (int64_t)gridDim.x * per_cta) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        warp_load_args(args, pl, cache, cached);
+        const KArgs<T> &a = *cache;
+        const int64_t local = wi - workoff[pl];
+        const int nsp = *a.nsub;
+        interp_warp2_item<T, W>(a, (int)(local % nsp), (int)(local / nsp), tile);
+    }
+}
+
+// One CTA per work item (3D staged tile, or unstaged GM-sort); the CTA shares
+// one KArgs copy.
+template <typename T, int DIM, int W, bool STAGED>
+__global__ void __launch_bounds__(256)
+interp_lane_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
+                         int nplans)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KArgs<T> *cache = reinterpret_cast<KArgs<T> *>(smem_raw);
+    auto *tile = reinterpret_cast<typename cplx<T>::type *>(smem_raw + args_slot<T>());
+    int cached = -1;
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        if (pl != cached) {
+            __syncthreads();
+            const int4 *src = reinterpret_cast<const int4 *>(args + pl);
+            int4 *dst = reinterpret_cast<int4 *>(cache);
+            for (int i = threadIdx.x; i < (int)(sizeof(KArgs<T>) / 16); i += blockDim.x)
+                dst[i] = src[i];
+            __syncthreads();
+            if (sizeof(T) == 4 && threadIdx.x == 0) cache->poly = 0;
+            __syncthreads();
+            cached = pl;
+        }
+        const KArgs<T> &a = *cache;
+        const int64_t local = wi - workoff[pl];
+        const int nsp = *a.nsub;
+        interp_lane_item<T, DIM, W, STAGED>(a, (int)(local % nsp), (int)(local / nsp), tile);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launch for one (T, DIM): picks the kernel for p.method and p.w.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -1455,18 +1588,19 @@ cudaError_t spread_w(Plan &p, const void *c)
     a.cin = reinterpret_cast<const typename cplx<T>::type *>(c);
     const int threads = p.threads;
     count_launch();
+    const int variant = sweep_variant(p);
     if constexpr (DIM == 3 && sizeof(T) == 4 && W <= 8) {
-        if (p.method == NUFFT_METHOD_SM && a.p0 <= 32 && (a.m2 == 1 || a.m2 == 2)) {
+        if (variant > 0) {
             cudaError_t e = cudaSuccess;
-            if (a.m2 == 1 ? launch_sweep3<T, W, 1>(p, a, &e) : launch_sweep3<T, W, 2>(p, a, &e))
+            if (variant == 1 ? launch_sweep3<T, W, 1>(p, a, &e) : launch_sweep3<T, W, 2>(p, a, &e))
                 return e;
         }
     }
-    if (p.method == NUFFT_METHOD_SM && DIM == 2 && a.p0 <= 32) {
+    if (DIM == 2 && variant > 0) {
         cudaError_t e = cudaSuccess;
-        if (a.p0 <= 8 ? launch_sweep2<T, W, 8>(p, a, threads, &e)
-                      : a.p0 <= 16 ? launch_sweep2<T, W, 16>(p, a, threads, &e)
-                                   : launch_sweep2<T, W, 32>(p, a, threads, &e))
+        if (variant == 8 ? launch_sweep2<T, W, 8>(p, a, threads, &e)
+                         : variant == 16 ? launch_sweep2<T, W, 16>(p, a, threads, &e)
+                                         : launch_sweep2<T, W, 32>(p, a, threads, &e))
             return e;
     }
     if (p.method == NUFFT_METHOD_SM) {
@@ -1531,24 +1665,61 @@ cudaError_t interp_w(Plan &p, void *c)
     return cudaGetLastError();
 }
 
+template <typename K>
+inline int multi_grid(K kernel, int threads, size_t smem, int num_sms)
+{
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    return num_sms * (per < 1 ? 1 : per);
+}
+
 template <typename T, int DIM, int W>
 cudaError_t spread_multi_w(const MultiLaunch &ml)
 {
     const auto *args = reinterpret_cast<const KArgs<T> *>(ml.args);
     count_launch();
+    if (ml.method == NUFFT_METHOD_SM && ml.variant > 0) {
+        if constexpr (DIM == 2) {
+            const size_t wb = sweep_bytes<T, W, 32>(kSweepCap, ml.m1max);
+            const size_t per = args_slot<T>() + wb;
+            int nw = 8;
+            while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
+            const size_t smem = per * nw;
+            auto launch = [&](auto k, int lanes_wb) {
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
+                    args, ml.workoff, ml.nplans, lanes_wb);
+            };
+            // the staging slots of the widest sub-warp form bound the narrower ones
+            if (ml.variant == 8) launch(spread_sweep2_multi_kernel<T, W, 8>, (int)wb);
+            else if (ml.variant == 16) launch(spread_sweep2_multi_kernel<T, W, 16>, (int)wb);
+            else launch(spread_sweep2_multi_kernel<T, W, 32>, (int)wb);
+            return cudaGetLastError();
+        } else if constexpr (sizeof(T) == 4 && W <= 8) {
+            const size_t wb = sweep3_bytes<T, W>(kSweepCap, ml.m1max);
+            const size_t per = args_slot<T>() + wb;
+            int nw = 4;
+            while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
+            const size_t smem = per * nw;
+            auto launch = [&](auto k) {
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
+                    args, ml.workoff, ml.nplans, (int)wb);
+            };
+            if (ml.variant == 1) launch(spread_sweep3_multi_kernel<T, W, 1>);
+            else launch(spread_sweep3_multi_kernel<T, W, 2>);
+            return cudaGetLastError();
+        }
+    }
     if (ml.method == NUFFT_METHOD_SM) {
         auto k = spread_sm_multi_kernel<T, DIM, W>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ml.smem);
-        int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, ml.threads, ml.smem);
-        k<<<ml.num_sms * (per < 1 ? 1 : per), ml.threads, ml.smem, ml.stream>>>(args, ml.workoff,
-                                                                                ml.nplans);
+        k<<<multi_grid(k, ml.threads, ml.smem, ml.num_sms), ml.threads, ml.smem, ml.stream>>>(
+            args, ml.workoff, ml.nplans);
     } else {
         auto k = spread_gmsort_multi_kernel<T, DIM, W>;
-        int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, ml.threads, 0);
-        k<<<ml.num_sms * (per < 1 ? 1 : per), ml.threads, 0, ml.stream>>>(args, ml.workoff,
-                                                                          ml.nplans);
+        k<<<multi_grid(k, ml.threads, 0, ml.num_sms), ml.threads, 0, ml.stream>>>(
+            args, ml.workoff, ml.nplans);
     }
     return cudaGetLastError();
 }
@@ -1556,21 +1727,33 @@ cudaError_t spread_multi_w(const MultiLaunch &ml)
 template <typename T, int DIM, int W>
 cudaError_t interp_multi_w(const MultiLaunch &ml)
 {
+    using C = typename cplx<T>::type;
     const auto *args = reinterpret_cast<const KArgs<T> *>(ml.args);
     count_launch();
+    if (ml.method == NUFFT_METHOD_SM && DIM == 2) {
+        const size_t per = args_slot<T>() + sizeof(C) * (size_t)ml.tile;
+        int nw = 8;
+        while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
+        if ((size_t)nw * per <= ml.smem_optin) {
+            const size_t smem = per * nw;
+            auto k = interp_warp2_multi_kernel<T, W>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
+                args, ml.workoff, ml.nplans, ml.tile);
+            return cudaGetLastError();
+        }
+    }
     if (ml.method == NUFFT_METHOD_SM) {
-        auto k = interp_sorted_multi_kernel<T, DIM, W, true>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ml.smem);
-        int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, ml.threads, ml.smem);
-        k<<<ml.num_sms * (per < 1 ? 1 : per), ml.threads, ml.smem, ml.stream>>>(args, ml.workoff,
-                                                                                ml.nplans);
+        const size_t smem = args_slot<T>() + sizeof(C) * (size_t)ml.tile;
+        auto k = interp_lane_multi_kernel<T, DIM, W, true>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<multi_grid(k, ml.threads, smem, ml.num_sms), ml.threads, smem, ml.stream>>>(
+            args, ml.workoff, ml.nplans);
     } else {
-        auto k = interp_sorted_multi_kernel<T, DIM, W, false>;
-        int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, ml.threads, 0);
-        k<<<ml.num_sms * (per < 1 ? 1 : per), ml.threads, 0, ml.stream>>>(args, ml.workoff,
-                                                                          ml.nplans);
+        const size_t smem = args_slot<T>();
+        auto k = interp_lane_multi_kernel<T, DIM, W, false>;
+        k<<<multi_grid(k, ml.threads, smem, ml.num_sms), ml.threads, smem, ml.stream>>>(
+            args, ml.workoff, ml.nplans);
     }
     return cudaGetLastError();
 }
