@@ -65,8 +65,8 @@ FP64_PEAK_TFLOPS = 1.25
 # kernel sources at capture time; a stale hash reports null.
 TRAFFIC = {
     # profiles/spread_interp_2d-1024-rand-eps1e-5.md
-    "spread:2d-1024-rand-eps1e-5:a0fe1669739a7c2b": 395570688,
-    "interp:2d-1024-rand-eps1e-5:a0fe1669739a7c2b": 312735488,
+    "spread:2d-1024-rand-eps1e-5:458daf3a997ac438": 406919936 + 37452800,
+    "interp:2d-1024-rand-eps1e-5:458daf3a997ac438": 252604160 + 47041024,
 }
 
 
