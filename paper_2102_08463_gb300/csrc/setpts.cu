@@ -267,8 +267,14 @@ column_scan_kernel(int32_t *__restrict__ mat, int nbins, int nblk, int32_t *__re
     }
 }
 
-// Counting sort, pass 3: stable ranked scatter of t.  The next tile's keys are
-// loaded before the current tile's slots are claimed.
+// Counting sort, pass 3: stable ranked scatter of t.  A tile is kRankU x 32
+// consecutive points per warp (warp w owns the w-th run of kRankU * 32); the
+// warps take turns, in warp order, to claim their slots, each turn placing its
+// kRankU chunks of 32 in order (ranks among equal keys by lane), so equal keys
+// keep their index order with one barrier per warp per tile.  The keys of the
+// next tile are loaded before the current tile's turns.
+constexpr int kRankU = 4;
+
 __global__ void __launch_bounds__(kCountThreads)
 rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restrict__ keys,
                     const int32_t *__restrict__ mat, const int32_t *__restrict__ binstart,
@@ -283,27 +289,48 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = min(beg + chunk, M);
     const unsigned lt_mask = (1u << lane) - 1u;
-    int64_t j = beg + threadIdx.x;
-    int key = j < end ? keys[j] : -1;
-    for (int64_t tile = beg; tile < end; tile += blockDim.x) {
-        const int64_t jn = j + blockDim.x;
-        const int keyn = jn < end ? keys[jn] : -1;
-        const unsigned peers = __match_any_sync(kFull, key);
-        const int lrank = __popc(peers & lt_mask);
-        const bool leader = key >= 0 && lrank == 0;
-        int base = 0;
-        // warps claim their slots in warp order: equal keys stay in index order
+    const int64_t tile = (int64_t)nwarps * 32 * kRankU;
+    const int64_t mine0 = (int64_t)warp * 32 * kRankU + lane;
+    int key[kRankU], keyn[kRankU];
+#pragma unroll
+    for (int u = 0; u < kRankU; ++u) {
+        const int64_t j = beg + mine0 + u * 32;
+        key[u] = j < end ? keys[j] : -1;
+    }
+    for (int64_t t0 = beg; t0 < end; t0 += tile) {
+#pragma unroll
+        for (int u = 0; u < kRankU; ++u) {
+            const int64_t j = t0 + tile + mine0 + u * 32;
+            keyn[u] = j < end ? keys[j] : -1;
+        }
+        unsigned peers[kRankU];
+        int base[kRankU];
+#pragma unroll
+        for (int u = 0; u < kRankU; ++u) {
+            peers[u] = __match_any_sync(kFull, key[u]);
+            base[u] = 0;
+        }
+        // only the slot claims are serialised, warp by warp
         for (int wv = 0; wv < nwarps; ++wv) {
-            if (warp == wv && leader) {
-                base = run[key];
-                run[key] = base + __popc(peers);
+            if (warp == wv) {
+#pragma unroll
+                for (int u = 0; u < kRankU; ++u) {
+                    if (key[u] >= 0 && (peers[u] & lt_mask) == 0) {
+                        base[u] = run[key[u]];
+                        run[key[u]] = base[u] + __popc(peers[u]);
+                    }
+                    __syncwarp();
+                }
             }
             __syncthreads();
         }
-        base = __shfl_sync(kFull, base, __ffs(peers) - 1);
-        if (key >= 0) perm[base + lrank] = (int32_t)j;
-        j = jn;
-        key = keyn;
+#pragma unroll
+        for (int u = 0; u < kRankU; ++u) {
+            const int b = __shfl_sync(kFull, base[u], __ffs(peers[u]) - 1);
+            if (key[u] >= 0) perm[b + __popc(peers[u] & lt_mask)] = (int32_t)(t0 + mine0 + u * 32);
+        }
+#pragma unroll
+        for (int u = 0; u < kRankU; ++u) key[u] = keyn[u];
     }
 }
 
