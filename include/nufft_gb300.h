@@ -66,7 +66,8 @@ typedef struct nufft_plan_s *nufft_plan;   /* opaque, library-owned */
 
 typedef struct {
     int    method;        /* NUFFT_METHOD_*; 0 = auto */
-    int    bin[3];        /* bin size m_i in fine-grid cells; 0 = default: 16x16x2 in 3D,
+    int    bin[3];        /* bin size m_i in fine-grid cells; 0 = default: 16x16x2 in 3D
+                             ((16 - w) x 16 x 2 for single-precision type 1 at w <= 4),
                              16x16 in 2D type 2; 2D type 1: (16 - w) x 16 single precision
                              ((8 - w) x 32 for w <= 3), (16 - w) x 32 double */
     int    msub;          /* max points per subproblem M_sub; 0 = default 1024 (Sec. 4.1 remark) */

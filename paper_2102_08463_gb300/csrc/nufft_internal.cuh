@@ -286,8 +286,8 @@ struct MultiLaunch {
     cudaStream_t stream;
 };
 // Row-sweep form of a type 1 SM plan (the batch's grouping key): 2D sub-warp
-// lanes 8, 16 or 32; 3D: 1 or 2 (bins one or two cells deep); 0 if the plan uses
-// the shared-memory atomic kernel.
+// lanes 8, 16 or 32; 3D: bin depth m2 (1 or 2), plus 4 for 16-lane sub-warps;
+// 0 if the plan uses the shared-memory atomic kernel.
 int sweep_variant(const Plan &p);
 cudaError_t spread_multi_f32_2d(const MultiLaunch &ml);
 cudaError_t spread_multi_f32_3d(const MultiLaunch &ml);

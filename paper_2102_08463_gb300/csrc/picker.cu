@@ -723,6 +723,7 @@ int nufft_picker_features(int type, int dim, const int64_t *nmodes, double eps, 
         nftot *= (double)nf;
         int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
         if (dim == 2 && type == 1) mdef = default_bin_2d_type1(d, prec, w);   // as makeplan
+        if (dim == 3 && type == 1 && prec == 0 && w <= 4 && d == 0) mdef = 16 - w;
         int m = tiles->bin[d] > 0 ? tiles->bin[d] : mdef;
         if (m > nf) m = (int)nf;
         t.bin[d] = m;

@@ -212,7 +212,7 @@ int nufft::sweep_variant(const Plan &p)
     const int p0 = padded(p.m[0], p.w);
     if (p0 > 32) return 0;
     if (p.dim == 2) return p0 <= 8 ? 8 : (p0 <= 16 ? 16 : 32);
-    if (p.prec == 0 && p.w <= 8 && (p.m[2] == 1 || p.m[2] == 2)) return p.m[2];
+    if (p.prec == 0 && p.w <= 8 && (p.m[2] == 1 || p.m[2] == 2)) return p.m[2] + (p0 <= 16 ? 4 : 0);
     return 0;
 }
 
@@ -359,6 +359,9 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
             p.nf[d] = next235(want);
             int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
             if (dim == 2 && type == 1) mdef = default_bin_2d_type1(d, prec, w);
+            // 3D single-precision type 1 at w <= 4: padded width in 16 lanes, so the
+            // 3D row sweep runs two points per warp step
+            if (dim == 3 && type == 1 && prec == 0 && w <= 4 && d == 0) mdef = 16 - w;
             int m = o.bin[d] > 0 ? o.bin[d] : mdef;
             if (m > p.nf[d]) m = (int)p.nf[d];
             if (padded(m, w) > 1023) { delete h; return NUFFT_ERR_ARG; }

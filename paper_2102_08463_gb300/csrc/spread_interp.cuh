@@ -278,10 +278,10 @@ template <typename T, int W, int L> __host__ __device__ constexpr int sweep2_slo
 {
     return ((quad_row<T, W>() + 2 * L / quad_vec<T>()) | 1) * quad_vec<T>();
 }
-// 3D slot: w_y, w_z, the L = 32 wide c w_x row, key word.
-template <typename T, int W> __host__ __device__ constexpr int sweep3_slot()
+// 3D slot: w_y, w_z, the L-wide c w_x row, key word.
+template <typename T, int W, int L> __host__ __device__ constexpr int sweep3_slot()
 {
-    return ((2 * quad_row<T, W>() + 64 / quad_vec<T>() + 1) | 1) * quad_vec<T>();
+    return ((2 * quad_row<T, W>() + 2 * L / quad_vec<T>() + 1) | 1) * quad_vec<T>();
 }
 
 __device__ __forceinline__ void store_zero_quad(float *dst)
@@ -328,15 +328,16 @@ constexpr int kSweepCap = 512;
 // (uint16) at 0, the row cursors at sweep_cur, the staging slots at sweep_head
 // (16-byte aligned).
 __host__ __device__ inline size_t sweep_cur(int msub) { return (size_t)4 * msub; }
-__host__ __device__ inline size_t sweep_head(int msub, int m1)
+// nkeys = number of distinct sort keys (2D: m1 + 1 start rows; 3D: (m1 + 1)(m2 + 1)).
+__host__ __device__ inline size_t sweep_head(int msub, int nkeys)
 {
-    return (sweep_cur(msub) + (size_t)4 * (m1 + 2) + 15) & ~(size_t)15;
+    return (sweep_cur(msub) + (size_t)4 * (nkeys + 1) + 15) & ~(size_t)15;
 }
 
 template <typename T, int W, int L>
 __host__ __device__ inline size_t sweep_bytes(int msub, int m1)
 {
-    return sweep_head(msub, m1) + sizeof(T) * (size_t)32 * sweep2_slot<T, W, L>();
+    return sweep_head(msub, m1 + 1) + sizeof(T) * (size_t)32 * sweep2_slot<T, W, L>();
 }
 
 // Single-precision ES kernel for the staging step, written without the
@@ -427,7 +428,7 @@ __device__ __forceinline__ void load_row(const double *s, double (&v)[W])
 // warp-aggregated integer atomics.  order[] receives the point indices grouped
 // by row, increasing index within a row.  One warp; cur[] holds nrow + 1
 // cursors.
-template <typename T>
+template <typename T, int ZMUL>
 __device__ __forceinline__ void sweep_row_sort(const typename rec4<T>::type *recs,
                                                const int32_t *perm, int n, int nrow,
                                                uint16_t *order, uint16_t *keys, int *cur)
@@ -446,7 +447,10 @@ __device__ __forceinline__ void sweep_row_sort(const typename rec4<T>::type *rec
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int k = base + u * 32 + lane;
-            if (k < n) keys[k] = (uint16_t)((w[u] >> 10) & 1023u);
+            // 2D: key = window start row; 3D: start row * (m2 + 1) + start plane
+            if (k < n)
+                keys[k] = (uint16_t)(ZMUL == 0 ? ((w[u] >> 10) & 1023u)
+                                               : ((w[u] >> 10) & 1023u) * ZMUL + (w[u] >> 20));
         }
     }
     __syncwarp();
@@ -498,12 +502,12 @@ __device__ __forceinline__ void spread_sweep2_piece(const KArgs<T> &a, int4 sub,
     uint16_t *order = reinterpret_cast<uint16_t *>(sm);
     uint16_t *keys = order + msub;
     int *cur = reinterpret_cast<int *>(sm + sweep_cur(msub));
-    T *stg = reinterpret_cast<T *>(sm + sweep_head(msub, a.m1));
+    T *stg = reinterpret_cast<T *>(sm + sweep_head(msub, a.m1 + 1));
     const int nrow = a.m1 + 1;                            // window start rows 0 .. m1
     const int32_t *perm = a.perm + sub.y;
 
     // 1. stable counting sort of the points by window start row
-    sweep_row_sort<T>(a.recs, perm, n, nrow, order, keys, cur);
+    sweep_row_sort<T, 0>(a.recs, perm, n, nrow, order, keys, cur);
 
     // 2.-4. stage and sweep; the next batch's gathers are issued before the
     // current batch is swept
@@ -600,17 +604,19 @@ __device__ __forceinline__ void spread_sweep2_piece(const KArgs<T> &a, int4 sub,
 
 // ---------------------------------------------------------------------------
 // Row-sweep SM spreading, 3D (single precision, W <= 8, bins m2 = M2 in {1, 2}).
-// As the 2D sweep with S = 1: lane q owns x column q of the padded bin, and
-// holds the W y rows in reach times all M2 + W z planes of the padded bin in
-// registers.  One point per warp step, so its window's first plane s_z is
-// warp-uniform and selects one of M2 + 1 unrolled updates
-//   acc[j][s_z + k] += (c w_x[q - s_x] w_y[j]) w_z[k],  j, k < W.
-// A finished row is added to the fine grid plane by plane.
+// As the 2D sweep: S = 32 / L sub-warps, lane q owns x column q of the padded
+// bin (p0 <= L) and holds the W y rows in reach times all M2 + W z planes in
+// registers.  The points are ordered by (window start row, start plane); the
+// points of one (row, plane) group are dealt to the sub-warps, so the first
+// plane s_z is the same for the whole warp and selects one of M2 + 1 unrolled
+// updates  acc[j][s_z + k] += (c w_x[q - s_x] w_y[j]) w_z[k],  j, k < W.
+// A finished row is summed over the sub-warps and added to the fine grid plane
+// by plane.
 // ---------------------------------------------------------------------------
-template <typename T, int W>
+template <typename T, int W, int M2, int L>
 __host__ __device__ inline size_t sweep3_bytes(int msub, int m1)
 {
-    return sweep_head(msub, m1) + sizeof(T) * (size_t)32 * sweep3_slot<T, W>();
+    return sweep_head(msub, (m1 + 1) * (M2 + 1)) + sizeof(T) * (size_t)32 * sweep3_slot<T, W, L>();
 }
 
 template <typename T, int W, int PZ, int O>
@@ -627,35 +633,36 @@ __device__ __forceinline__ void sweep3_add(T (&ar)[W][PZ], T (&ai)[W][PZ], const
     }
 }
 
-template <typename T, int W, int M2>
+template <typename T, int W, int M2, int L>
 __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub, int tr,
                                                     unsigned char *sm)
 {
     constexpr int msub = kSweepCap;
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
+    constexpr int S = 32 / L;
     constexpr int PZ = M2 + W;
-    constexpr int SLOT = sweep3_slot<T, W>();
+    constexpr int SLOT = sweep3_slot<T, W, L>();
     constexpr int RW = quad_row<T, W>() * quad_vec<T>();
-    constexpr int OWY = 0, OWZ = RW, OCX = 2 * RW, OKEY = 2 * RW + 64;
-    const int lane = threadIdx.x & 31;
+    constexpr int OWY = 0, OWZ = RW, OCX = 2 * RW, OKEY = 2 * RW + 2 * L;
+    const int lane = threadIdx.x & 31, h = lane / L, q = lane % L;
     const int n = sub.z;
     uint16_t *order = reinterpret_cast<uint16_t *>(sm);
     uint16_t *keys = order + msub;
     int *cur = reinterpret_cast<int *>(sm + sweep_cur(msub));
-    T *stg = reinterpret_cast<T *>(sm + sweep_head(msub, a.m1));
-    const int nrow = a.m1 + 1;
+    const int nkeys = (a.m1 + 1) * (M2 + 1);
+    T *stg = reinterpret_cast<T *>(sm + sweep_head(msub, nkeys));
     const int32_t *perm = a.perm + sub.y;
 
-    sweep_row_sort<T>(a.recs, perm, n, nrow, order, keys, cur);
+    sweep_row_sort<T, M2 + 1>(a.recs, perm, n, nkeys, order, keys, cur);
 
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
     const int P = pad_lo(W);
     const C *cin = a.cin + (int64_t)tr * a.M;
     C *grid = a.grid + (int64_t)tr * a.nftot;
-    const bool writer = lane < a.p0;
-    const int gx = wrap_any(o0 - P + (writer ? lane : 0), a.n0);
+    const bool writer = h == 0 && q < a.p0;
+    const int gx = wrap_any(o0 - P + (q < a.p0 ? q : 0), a.n0);
     const int row0 = o1 - P, plane0 = o2 - P;
     T accr[W][PZ], acci[W][PZ];
 #pragma unroll
@@ -664,7 +671,15 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
         for (int k = 0; k < PZ; ++k) accr[j][k] = acci[j][k] = (T)0;
     int row = 0;
 
-    auto flush_row = [&](int r_rel, const T (&vr)[PZ], const T (&vi)[PZ]) {
+    auto flush_row = [&](int r_rel, T (&vr)[PZ], T (&vi)[PZ]) {
+#pragma unroll
+        for (int k = 0; k < PZ; ++k) {
+#pragma unroll
+            for (int o = L; o < 32; o <<= 1) {
+                vr[k] += __shfl_xor_sync(kFullMask, vr[k], o);
+                vi[k] += __shfl_xor_sync(kFullMask, vi[k], o);
+            }
+        }
         if (!writer) return;
         const int gy = wrap_any(row0 + r_rel, a.n1);
 #pragma unroll
@@ -688,11 +703,11 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
     fetch(0);
     for (int base = 0; base < n; base += 32) {
         const int cnt = min(32, n - base);
-        int myrow = 0x7fffffff;
+        int mykey = 0x7fffffff;
         if (lane < cnt) {
             const uint32_t pk = unpack_word<T>(rc.w);
             T *s = stg + lane * SLOT;
-            myrow = (int)((pk >> 10) & 1023u);
+            mykey = (int)((pk >> 10) & 1023u) * (M2 + 1) + (int)(pk >> 20);
             reinterpret_cast<uint32_t *>(s + OKEY)[0] = pk >> 20;
             const int sx = (int)(pk & 1023u);
             T vx[W], vy[W], vz[W];
@@ -700,7 +715,7 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
             kernel_row<T, W>(a, rc.y, vy);
             kernel_row<T, W>(a, rc.z, vz);
 #pragma unroll
-            for (int k = 0; k < 64; k += quad_vec<T>()) store_zero_quad(s + OCX + k);
+            for (int k = 0; k < 2 * L; k += quad_vec<T>()) store_zero_quad(s + OCX + k);
 #pragma unroll
             for (int i = 0; i < W; ++i) {
                 C v;
@@ -715,8 +730,9 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
         __syncwarp();
         int i0 = 0;
         while (i0 < cnt) {
-            const int r = __shfl_sync(kFullMask, myrow, i0);
-            while (row < r) {
+            const int r = __shfl_sync(kFullMask, mykey, i0);
+            const int rrow = r / (M2 + 1);
+            while (row < rrow) {
                 flush_row(row, accr[0], acci[0]);
 #pragma unroll
                 for (int j = 0; j + 1 < W; ++j)
@@ -729,12 +745,12 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
                 for (int k = 0; k < PZ; ++k) accr[W - 1][k] = acci[W - 1][k] = (T)0;
                 ++row;
             }
-            const unsigned later = __ballot_sync(kFullMask, myrow > r) & ~((2u << i0) - 1u);
+            const unsigned later = __ballot_sync(kFullMask, mykey > r) & ~((2u << i0) - 1u);
             const int i1 = later ? __ffs(later) - 1 : cnt;
-            for (int i = i0; i < i1; ++i) {
+            const int sz = r - rrow * (M2 + 1);             // the group's first plane
+            for (int i = i0 + h; i < i1; i += S) {
                 const T *s = stg + i * SLOT;
-                const int sz = (int)reinterpret_cast<const uint32_t *>(s + OKEY)[0];
-                const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * lane);
+                const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * q);
                 const T wr = cx.x, wi = cx.y;
                 T wy[W], wz[W], t[W], u[W];
                 load_row<W>(s + OWY, wy);
@@ -760,17 +776,17 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
 }
 
 // A subproblem in pieces of at most kSweepCap points (sub = {bin, start, count}).
-template <typename T, int W, int M2>
+template <typename T, int W, int M2, int L>
 __device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, int tr,
                                                    unsigned char *sm)
 {
     const int4 sub = a.subprob[sp];
     for (int piece = 0; piece < sub.z; piece += kSweepCap)
-        spread_sweep3_piece<T, W, M2>(
+        spread_sweep3_piece<T, W, M2, L>(
             a, make_int4(sub.x, sub.y + piece, min(kSweepCap, sub.z - piece), 0), tr, sm);
 }
 
-template <typename T, int W, int M2>
+template <typename T, int W, int M2, int L>
 __global__ void __launch_bounds__(128)
 spread_sweep3_kernel(KArgs<T> a, int warp_bytes)
 {
@@ -782,7 +798,7 @@ spread_sweep3_kernel(KArgs<T> a, int warp_bytes)
     const int64_t nwork = (int64_t)nsp * a.ntransf;
     for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
          wi += (int64_t)gridDim.x * per_cta)
-        spread_sweep3_item<T, W, M2>(a, (int)(wi % nsp), (int)(wi / nsp), sm);
+        spread_sweep3_item<T, W, M2, L>(a, (int)(wi % nsp), (int)(wi / nsp), sm);
 }
 
 template <typename T, int W, int L>
@@ -1418,7 +1434,7 @@ spread_sweep2_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__r
     }
 }
 
-template <typename T, int W, int M2>
+template <typename T, int W, int M2, int L>
 __global__ void __launch_bounds__(128)
 spread_sweep3_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
                            int nplans, int warp_bytes)
@@ -1438,7 +1454,7 @@ spread_sweep3_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__r
         const KArgs<T> &a = *cache;
         const int64_t local = wi - workoff[pl];
         const int nsp = *a.nsub;
-        spread_sweep3_item<T, W, M2>(a, (int)(local % nsp), (int)(local / nsp), sm);
+        spread_sweep3_item<T, W, M2, L>(a, (int)(local % nsp), (int)(local / nsp), sm);
     }
 }
 
@@ -1566,15 +1582,15 @@ bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
     return true;
 }
 
-template <typename T, int W, int M2>
+template <typename T, int W, int M2, int L>
 bool launch_sweep3(Plan &p, const KArgs<T> &a, cudaError_t *err)
 {
-    const size_t warp_bytes = sweep3_bytes<T, W>(kSweepCap, a.m1);
+    const size_t warp_bytes = sweep3_bytes<T, W, M2, L>(kSweepCap, a.m1);
     int nw = 4;
     while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
     if (nw < 2) return false;
     const size_t smem = warp_bytes * nw;
-    auto k = spread_sweep3_kernel<T, W, M2>;
+    auto k = spread_sweep3_kernel<T, W, M2, L>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, (int)warp_bytes);
     *err = cudaGetLastError();
@@ -1592,8 +1608,12 @@ cudaError_t spread_w(Plan &p, const void *c)
     if constexpr (DIM == 3 && sizeof(T) == 4 && W <= 8) {
         if (variant > 0) {
             cudaError_t e = cudaSuccess;
-            if (variant == 1 ? launch_sweep3<T, W, 1>(p, a, &e) : launch_sweep3<T, W, 2>(p, a, &e))
-                return e;
+            // variant: m2 (1 or 2), plus 4 when the padded width fits 16 lanes
+            const bool ok = variant == 1   ? launch_sweep3<T, W, 1, 32>(p, a, &e)
+                            : variant == 2 ? launch_sweep3<T, W, 2, 32>(p, a, &e)
+                            : variant == 5 ? launch_sweep3<T, W, 1, 16>(p, a, &e)
+                                           : launch_sweep3<T, W, 2, 16>(p, a, &e);
+            if (ok) return e;
         }
     }
     if (DIM == 2 && variant > 0) {
@@ -1696,7 +1716,7 @@ cudaError_t spread_multi_w(const MultiLaunch &ml)
             else launch(spread_sweep2_multi_kernel<T, W, 32>, (int)wb);
             return cudaGetLastError();
         } else if constexpr (sizeof(T) == 4 && W <= 8) {
-            const size_t wb = sweep3_bytes<T, W>(kSweepCap, ml.m1max);
+            const size_t wb = sweep3_bytes<T, W, 2, 32>(kSweepCap, ml.m1max);
             const size_t per = args_slot<T>() + wb;
             int nw = 4;
             while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
@@ -1706,8 +1726,10 @@ cudaError_t spread_multi_w(const MultiLaunch &ml)
                 k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
                     args, ml.workoff, ml.nplans, (int)wb);
             };
-            if (ml.variant == 1) launch(spread_sweep3_multi_kernel<T, W, 1>);
-            else launch(spread_sweep3_multi_kernel<T, W, 2>);
+            if (ml.variant == 1) launch(spread_sweep3_multi_kernel<T, W, 1, 32>);
+            else if (ml.variant == 2) launch(spread_sweep3_multi_kernel<T, W, 2, 32>);
+            else if (ml.variant == 5) launch(spread_sweep3_multi_kernel<T, W, 1, 16>);
+            else launch(spread_sweep3_multi_kernel<T, W, 2, 16>);
             return cudaGetLastError();
         }
     }

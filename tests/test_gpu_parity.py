@@ -163,7 +163,9 @@ def test_sweep_spread_matches_oracle(nb, bins, msub, eps, prec, kind, nt):
     ((16, 16, 2), 1024, 1e-6, "rand", 1),      # w = 7
     ((16, 8, 1), 128, 1e-5, "cluster", 1),     # w = 6, m2 = 1, many subproblems per bin
     ((25, 16, 2), 512, 1e-2, "gauss", 2),      # w = 3, widest bins, ntransf 2
-    ((8, 16, 2), 64, 1e-4, "rand", 1),         # w = 5
+    ((8, 16, 2), 64, 1e-4, "rand", 1),         # w = 5, 16-lane sub-warps
+    ((9, 16, 2), 256, 1e-6, "gauss", 1),       # w = 7, 16-lane sub-warps
+    ((13, 8, 1), 96, 1e-2, "cluster", 1),      # w = 3, 16-lane sub-warps, m2 = 1
 ])
 def test_sweep3_spread_matches_oracle(nb, bins, msub, eps, kind, nt):
     N = (26, 22, 20)
