@@ -64,8 +64,9 @@ int cuda_rc(cudaError_t e)
 
 }  // namespace
 
-std::vector<Tiles> nufft::tile_candidates(int dim)
+std::vector<Tiles> nufft::tile_candidates(const Plan &p)
 {
+    const int dim = p.dim;
     std::vector<std::vector<int>> bins;
     if (dim == 2)
         bins = {{8, 8, 1}, {16, 16, 1}, {32, 16, 1}, {32, 32, 1}, {64, 32, 1}};
@@ -92,6 +93,17 @@ std::vector<Tiles> nufft::tile_candidates(int dim)
     gm.bin[0] = gm.bin[1] = 16;
     gm.bin[2] = dim == 3 ? 2 : 1;
     out.push_back(gm);
+    // the plan's default (heuristic) tiling, when not already listed
+    Tiles h;
+    h.method = NUFFT_METHOD_SM;
+    default_bins(p.type, dim, p.prec, p.w, h.bin);
+    h.msub = 1024;
+    h.threads = kDefaultThreads;
+    bool listed = false;
+    for (const Tiles &t : out)
+        listed = listed || (t.method == h.method && t.bin[0] == h.bin[0] && t.bin[1] == h.bin[1] &&
+                            t.bin[2] == h.bin[2] && t.msub == h.msub && t.threads == h.threads);
+    if (!listed) out.push_back(h);
     return out;
 }
 
@@ -132,7 +144,7 @@ int nufft_autotune(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     double best_time = 1e300;
     Tiles best_t;
     int n = 0;
-    for (const Tiles &t : tile_candidates(p.dim)) {
+    for (const Tiles &t : tile_candidates(p)) {
         if (plan_set_tiles(p, t) != NUFFT_OK) continue;
         cudaEventRecord(e0, p.stream);
         if (nufft_setpts(h, M, x, y, z) != NUFFT_OK) continue;

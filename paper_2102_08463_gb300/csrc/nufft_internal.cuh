@@ -30,6 +30,16 @@ inline int default_bin_2d_type1(int axis, int prec, int w)
     if (axis == 0) return w <= 15 ? 16 - w : 32 - w;
     return prec == 0 ? 16 : 32;
 }
+// Default bin sizes of a plan (1 on unused axes): 16 x 16 (2D) and 16 x 16 x 2
+// (3D), with the row-sweep sizes above for 2D type 1 and, for 3D single-precision
+// type 1 at w <= 4, 16 - w cells in x (16-lane sub-warps).
+inline void default_bins(int type, int dim, int prec, int w, int out[3])
+{
+    for (int d = 0; d < 3; ++d) out[d] = d < dim ? (dim == 2 ? 16 : (d < 2 ? 16 : 2)) : 1;
+    if (dim == 2 && type == 1)
+        for (int d = 0; d < 2; ++d) out[d] = default_bin_2d_type1(d, prec, w);
+    if (dim == 3 && type == 1 && prec == 0 && w <= 4) out[0] = 16 - w;
+}
 // Degree of the kernel polynomials: enough for 2e-8 (single) / 1e-14 (double)
 // on the interior window cells at every width.
 __host__ __device__ constexpr int poly_degree(int prec) { return prec == 0 ? 10 : 16; }
@@ -230,8 +240,10 @@ int plan_set_tiles(Plan &p, const Tiles &t);
 bool tiles_feasible(const Plan &p, const Tiles &t);
 // Tuned tiles for this plan and M from the autotuner's cache, if any.
 bool tune_cache_lookup(const Plan &p, int64_t M, Tiles *out);
-// The candidate tilings the autotuner times and the picker ranks, in a fixed order.
-std::vector<Tiles> tile_candidates(int dim);
+// The candidate tilings the autotuner times and the picker ranks, in a fixed
+// order: a grid of bins x M_sub x threads for SM and GM-sort, one GM entry, and
+// the plan's default tiling when the grid does not contain it.
+std::vector<Tiles> tile_candidates(const Plan &p);
 // Tiles chosen by the installed picker for this plan and these points.  Sets
 // *chosen = false (and returns NUFFT_OK) when no picker is installed.
 // Synchronizes p.stream.

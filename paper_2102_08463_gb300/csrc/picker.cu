@@ -478,7 +478,7 @@ int nufft::picker_choose(Plan &p, int64_t M, const void *x, const void *y, const
     int rc = point_skew(p.dim, p.prec, M, x, y, z, h->hist, &skew, p.stream);
     if (rc != NUFFT_OK) return rc;
     std::vector<Tiles> cand;
-    for (const Tiles &t : tile_candidates(p.dim))
+    for (const Tiles &t : tile_candidates(p))
         if (tiles_feasible(p, t)) cand.push_back(t);
     if (cand.empty()) return NUFFT_OK;
     const int64_t nc = (int64_t)cand.size();
@@ -721,9 +721,9 @@ int nufft_picker_features(int type, int dim, const int64_t *nmodes, double eps, 
         if (want < 2 * w) want = 2 * w;
         const int64_t nf = next235(want);
         nftot *= (double)nf;
-        int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
-        if (dim == 2 && type == 1) mdef = default_bin_2d_type1(d, prec, w);   // as makeplan
-        if (dim == 3 && type == 1 && prec == 0 && w <= 4 && d == 0) mdef = 16 - w;
+        int defb[3];
+        default_bins(type, dim, prec, w, defb);            // as makeplan
+        const int mdef = defb[d];
         int m = tiles->bin[d] > 0 ? tiles->bin[d] : mdef;
         if (m > nf) m = (int)nf;
         t.bin[d] = m;

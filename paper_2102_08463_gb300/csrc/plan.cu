@@ -357,11 +357,9 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
             int64_t want = (int64_t)ceil(sigma * (double)p.N[d] - 1e-9);
             if (want < 2 * w) want = 2 * w;
             p.nf[d] = next235(want);
-            int mdef = dim == 2 ? 16 : (d < 2 ? 16 : 2);
-            if (dim == 2 && type == 1) mdef = default_bin_2d_type1(d, prec, w);
-            // 3D single-precision type 1 at w <= 4: padded width in 16 lanes, so the
-            // 3D row sweep runs two points per warp step
-            if (dim == 3 && type == 1 && prec == 0 && w <= 4 && d == 0) mdef = 16 - w;
+            int defb[3];
+            default_bins(type, dim, prec, w, defb);
+            const int mdef = defb[d];
             int m = o.bin[d] > 0 ? o.bin[d] : mdef;
             if (m > p.nf[d]) m = (int)p.nf[d];
             if (padded(m, w) > 1023) { delete h; return NUFFT_ERR_ARG; }
