@@ -666,13 +666,83 @@ def run_picker_bench(args):
     }
 
 
+def run_method_sweep(args):
+    """The paper's method comparison (spreading and interpolation time per point of
+    GM, GM-sort and SM against the fine-grid size, uniform and box-clustered points,
+    densities 0.1, 1, 10), 2D single precision at eps = 1e-5, on this GPU.  Sizes
+    with more than 2^24 points are left out; each time is the median of 5 launches
+    (L2 flushed before each)."""
+    import torch
+    from paper_2102_08463_gb300 import binding
+
+    torch.cuda.set_device(0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ts.sort()
+        return ts[len(ts) // 2]
+
+    rows = []
+    launches0 = binding.get_launch_count()
+    for n in (256, 512, 1024, 2048, 4096):
+        for rho in (0.1, 1.0, 10.0):
+            M = int(round(rho * n * n))
+            if M > (1 << 24):
+                continue
+            for kind in ("rand", "cluster"):
+                N = (n // 2, n // 2)
+                pts = [torch.from_numpy(a).cuda()
+                       for a in wl.points(kind, 2, M, SEED + 77, np.float32, n=(n, n))]
+                c = torch.from_numpy(wl.strengths(M, SEED + 78, np.complex64)).cuda()
+                co = torch.empty_like(c)
+                row = {"n": n, "rho": rho, "M": M, "dist": kind}
+                for method in ("gm", "gmsort", "sm"):
+                    p1 = binding.Plan(1, N, 1e-5, prec=0, method=method)
+                    p1.setpts(*pts)
+                    t_s = timed(lambda: binding.spread_add(p1.handle, binding._dptr(c)))
+                    t_set = timed(lambda: p1.setpts(*pts))
+                    p1.close()
+                    p2 = binding.Plan(2, N, 1e-5, prec=0, method=method)
+                    p2.setpts(*pts)
+                    t_i = timed(lambda: binding.interp(p2.handle, binding._dptr(co)))
+                    p2.close()
+                    row[method] = {"spread_ns_per_pt": round(t_s * 1e6 / M, 4),
+                                   "interp_ns_per_pt": round(t_i * 1e6 / M, 4),
+                                   "setpts_ns_per_pt": round(t_set * 1e6 / M, 4)}
+                rows.append(row)
+                del pts, c, co
+    launches = binding.get_launch_count() - launches0
+    sm = [r["sm"]["spread_ns_per_pt"] for r in rows if r["rho"] == 1.0 and r["dist"] == "rand"]
+    return {
+        "metric": "2D spread / interp ns per point by method (GM, GM-sort, SM) vs fine grid",
+        "value": round(min(sm), 4) if sm else None, "unit": "ns/pt (SM spread, rho=1 rand, best n)",
+        "n_gpus": 1, "steps": 5, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded SplitMix64: uniform on [-pi,pi)^2 and the box [0, 8h]^2)",
+        "config": {"workload": "method-sweep: 2D eps=1e-5 complex64, fine grid n^2 for n in "
+                               "256..4096, density M/n^2 in {0.1, 1, 10} (M <= 2^24)"},
+        "gpu_launches": int(launches),
+        "table": rows,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=sorted(WORKLOADS) + ["batch-256", "picker-holdout"])
+                    choices=sorted(WORKLOADS) + ["batch-256", "picker-holdout", "method-sweep"])
     ap.add_argument("--picker-problems", type=int, default=24)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--method1", default="auto")
@@ -688,6 +758,9 @@ def main():
         return
     if args.workload == "picker-holdout":
         print(json.dumps(run_picker_bench(args)), flush=True)
+        return
+    if args.workload == "method-sweep":
+        print(json.dumps(run_method_sweep(args)), flush=True)
         return
     W = dict(WORKLOADS[args.workload])
 
