@@ -2,24 +2,22 @@
 // interpolation (type 2 step 3, Sec. 3.2 / Sec. 4.2) kernels, templated on the
 // precision T, the dimension DIM and the kernel width W.
 //
-// Thread mapping shared by the kernels here: a warp is cut into G = 32 / W lane
-// groups of W lanes; group g works on one point, lane dx of the group owns
-// window column dx.  Each lane evaluates the ES kernel only for its own column
-// in x, y (and z) -- d evaluations per lane instead of d*W per thread -- and
-// hands the y / z weights to the rest of its group by shuffles, once per point.
-// The bin-ordered kernels first load a batch of 32 points per warp (one point
-// per lane: index from t, then its record and strength) and then feed the groups from registers by
-// shuffles, so one memory round trip serves 32 points.
-//
-//   SM       Sec. 4.1 SM steps 1-3: one CTA per (subproblem, transform); points
-//            accumulate into a shared-memory copy of the padded bin
-//            (m_i + w cells per axis) with shared atomics, then the padded bin is
-//            atomically added to the fine grid with periodic wrap.
-//   GM-sort  the same bin-ordered points, atomics straight into the fine grid.
-//   GM       user order, positions recomputed from the coordinates.
-//   interp   the transpose: each group gathers its point's w^d cells (from the
-//            padded bin staged in shared memory, or from the fine grid) and the
-//            W column sums are combined with shuffles.
+//   SM spreading   the row sweeps (spread_sweep2 / spread_sweep3): one warp per
+//                  subproblem, lanes own the columns of the padded bin, the rows a
+//                  window reaches are registers, finished rows are reduced into
+//                  the fine grid -- no shared-memory atomics.  Bins too wide for 32
+//                  lanes (and 3D double precision) use spread_sm_kernel: the padded
+//                  bin in shared memory with shared atomics, then added to the fine
+//                  grid (Sec. 4.1 SM steps 1-3).
+//   GM-sort / GM   bin-ordered / user-order points, reductions straight into the
+//                  fine grid; a warp is cut into G = 32 / W lane groups, group g
+//                  works on one point, lane dx owns window column dx.
+//   interpolation  one thread per point: the padded bin is staged in shared memory
+//                  (SM; one warp per subproblem in 2D) or read from the fine grid
+//                  (GM-sort), each lane sums its own point's W^d window; GM
+//                  interpolation uses the lane groups.
+// Kernel values come from kernel_row: piecewise polynomials for the interior
+// window cells, the ES formula for the two edge cells.
 #pragma once
 
 #include "nufft_internal.cuh"
@@ -267,10 +265,6 @@ template <typename T> __host__ __device__ constexpr int quad_vec() { return 16 /
 template <typename T, int W> __host__ __device__ constexpr int quad_row()
 {
     return (W + quad_vec<T>() - 1) / quad_vec<T>();
-}
-template <typename T, int W, int ROWS> __host__ __device__ constexpr int sweep_slot_t()
-{
-    return (((ROWS * quad_row<T, W>() + 1) | 1) * quad_vec<T>());
 }
 // 2D slot: w_y row, then c w_x scattered into an L-wide complex row (zeros
 // outside the window), so lane q reads entry q at a fixed address.
@@ -992,128 +986,6 @@ __device__ __forceinline__ T group_sum(T v, int dx)
 }
 
 // ---------------------------------------------------------------------------
-// Sorted interpolation (GM-sort, Sec. 4.2) and its shared-memory staged form
-// (STAGED = true): the padded bin of the subproblem is first copied into
-// shared memory with coalesced row loads, then every gather reads it there.
-// Each group's total lands on lane dx == 0 and is handed to the lane that
-// loaded the point, so the batch writes its 32 results together.
-// ---------------------------------------------------------------------------
-template <typename T, int DIM, int W, bool STAGED>
-__device__ __forceinline__ void interp_sorted_item(const KArgs<T> &a, int sp, int tr,
-                                                   typename cplx<T>::type *tile)
-{
-    using C = typename cplx<T>::type;
-    using R = typename rec4<T>::type;
-    constexpr int G = 32 / W;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int g = lane / W, dx = lane - (lane / W) * W;
-    const bool gact = g < G;
-    const int src0 = (gact ? g : G - 1) * W;
-    const int P = pad_lo(W);
-    const int p01 = a.p0 * a.p1;
-    {
-        const int4 sub = a.subprob[sp];
-        int o0, o1, o2;
-        bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
-        const C *grid = a.grid + (int64_t)tr * a.nftot;
-        C *cout = a.cout + (int64_t)tr * a.M;
-        if (STAGED) {
-            const int rows = a.p1 * (DIM == 3 ? a.p2 : 1);
-            for (int rr = warp; rr < rows; rr += nwarps) {
-                const int ry = rr % a.p1, rz = rr / a.p1;
-                const int gy = wrap_any(o1 - P + ry, a.n1);
-                const int gz = DIM == 3 ? wrap_any(o2 - P + rz, a.n2) : 0;
-                const C *src = grid + ((int64_t)gz * a.n1 + gy) * a.n0;
-                for (int rx = lane; rx < a.p0; rx += 32)
-                    tile[rr * a.p0 + rx] = src[wrap_any(o0 - P + rx, a.n0)];
-            }
-            __syncthreads();
-        }
-        for (int base = warp * 32; base < sub.z; base += nwarps * 32) {
-            R r;
-            r.x = r.y = r.z = r.w = (T)0;
-            C dummy;
-            dummy.x = dummy.y = (T)0;
-            int myperm = 0;
-            if (base + lane < sub.z) {
-                myperm = a.perm[sub.y + base + lane];
-                r = a.recs[myperm];
-            }
-            const int np = min(32, sub.z - base);
-            C res;
-            res.x = res.y = (T)0;
-            for (int i0 = 0; i0 < np; i0 += G) {
-                const int p = i0 + g;
-                const bool act = gact && p < np;
-                const PointView<T> pv = take_point<T, false>(r, dummy, p < 32 ? p : 31);
-                const T wx = es_kernel(((T)dx - pv.dx) * a.hw, a.beta);
-                const T myy = es_kernel(((T)dx - pv.dy) * a.hw, a.beta);
-                const T myz = DIM == 3 ? es_kernel(((T)dx - pv.dz) * a.hw, a.beta) : (T)0;
-                T wy[W];
-#pragma unroll
-                for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
-                const int sx = pv.pk & 1023u, sy = (pv.pk >> 10) & 1023u, sz = pv.pk >> 20;
-                T ar = 0, ai = 0;
-                const int nz = DIM == 3 ? W : 1;
-                if (STAGED) {
-                    const int baddr = act ? (sz * a.p1 + sy) * a.p0 + sx + dx : 0;
-#pragma unroll 1
-                    for (int iz = 0; iz < nz; ++iz) {
-                        const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
-                        int addr = baddr + iz * p01;
-                        T zr = 0, zi = 0;
-#pragma unroll
-                        for (int iy = 0; iy < W; ++iy) {
-                            const C t = tile[addr];
-                            zr += wy[iy] * t.x;
-                            zi += wy[iy] * t.y;
-                            addr += a.p0;
-                        }
-                        ar += vz * zr;
-                        ai += vz * zi;
-                    }
-                } else {
-                    const int gx = wrap_any(o0 - P + sx + dx, a.n0);
-#pragma unroll 1
-                    for (int iz = 0; iz < nz; ++iz) {
-                        const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
-                        const int gz = DIM == 3 ? wrap_any(o2 - P + sz + iz, a.n2) : 0;
-                        T zr = 0, zi = 0;
-#pragma unroll
-                        for (int iy = 0; iy < W; ++iy) {
-                            if (act) {
-                                const int gy = wrap_any(o1 - P + sy + iy, a.n1);
-                                const C t = grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx];
-                                zr += wy[iy] * t.x;
-                                zi += wy[iy] * t.y;
-                            }
-                        }
-                        ar += vz * zr;
-                        ai += vz * zi;
-                    }
-                }
-                ar = act ? ar * wx : (T)0;
-                ai = act ? ai * wx : (T)0;
-                ar = group_sum<T, W>(ar, dx);
-                ai = group_sum<T, W>(ai, dx);
-                // group totals sit on lanes j*W; hand point i0+j's total to lane i0+j
-#pragma unroll
-                for (int j = 0; j < G; ++j) {
-                    const T tr_ = shfl(ar, j * W), ti_ = shfl(ai, j * W);
-                    if (lane == i0 + j) {
-                        res.x = tr_;
-                        res.y = ti_;
-                    }
-                }
-            }
-            if (lane < np) cout[myperm] = res;
-        }
-        if (STAGED) __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Sorted interpolation with one thread per point (Sec. 4.2).  The CTA stages
 // the subproblem's padded bin in shared memory (STAGED; coalesced row loads
 // with periodic wrap) or reads the fine grid directly (GM-sort), then every
@@ -1281,35 +1153,6 @@ interp_lane_kernel(KArgs<T> a)
     const int64_t nwork = (int64_t)nsp * a.ntransf;
     for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x)
         interp_lane_item<T, DIM, W, STAGED>(a, (int)(wi % nsp), (int)(wi / nsp), tile);
-}
-
-template <typename T, int DIM, int W, bool STAGED>
-__global__ void __launch_bounds__(256)
-interp_sorted_kernel(KArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto *tile = reinterpret_cast<typename cplx<T>::type *>(smem_raw);
-    const int nsp = *a.nsub;
-    const int64_t nwork = (int64_t)nsp * a.ntransf;
-    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x)
-        interp_sorted_item<T, DIM, W, STAGED>(a, (int)(wi % nsp), (int)(wi / nsp), tile);
-}
-
-template <typename T, int DIM, int W, bool STAGED>
-__global__ void __launch_bounds__(256)
-interp_sorted_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
-                           int nplans)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto *tile = reinterpret_cast<typename cplx<T>::type *>(smem_raw);
-    const int64_t nwork = workoff[nplans];
-    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-        const int pl = batch_plan_of(workoff, nplans, wi);
-        const KArgs<T> &a = args[pl];
-        const int64_t local = wi - workoff[pl];
-        const int nsp = *a.nsub;
-        interp_sorted_item<T, DIM, W, STAGED>(a, (int)(local % nsp), (int)(local / nsp), tile);
-    }
 }
 
 // ---------------------------------------------------------------------------
