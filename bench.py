@@ -64,9 +64,10 @@ FP64_PEAK_TFLOPS = 1.25
 # dram__bytes_write.sum), keyed by kernel and workload, with the hash of the
 # kernel sources at capture time; a stale hash reports null.
 TRAFFIC = {
-    # profiles/spread_interp_2d-1024-rand-eps1e-5.md
-    "spread:2d-1024-rand-eps1e-5:458daf3a997ac438": 406919936 + 37452800,
-    "interp:2d-1024-rand-eps1e-5:458daf3a997ac438": 252604160 + 47041024,
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --metrics, bench command
+    # of profiles/launches_2d-1024-rand-eps1e-5.md with -k spread_sweep2|interp_warp2)
+    "spread:2d-1024-rand-eps1e-5:ab4b7cf43a23f50e": 443805440,
+    "interp:2d-1024-rand-eps1e-5:ab4b7cf43a23f50e": 298646272,
 }
 
 
