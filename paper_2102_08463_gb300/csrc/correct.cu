@@ -15,6 +15,8 @@ namespace nufft {
 
 namespace {
 
+constexpr int kPerThread = 4;   // row elements per thread in the correction kernels
+
 // One thread per mode: rows of N1 along threadIdx/blockIdx.x, one grid row
 // (k2, k3, transform) per blockIdx.y/z slot.
 template <typename T>
@@ -38,15 +40,23 @@ __global__ void deconvolve_kernel(const typename cplx<T>::type *__restrict__ gri
         const T s = p1[i1] * p2[i2];
         const C *src = grid + (int64_t)tr * nftot + ((int64_t)l2 * n1 + l1) * n0;
         C *dst = f + (int64_t)tr * Ntot + ((int64_t)i2 * N1 + i1) * N0;
-        for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < N0; i0 += gridDim.x * blockDim.x) {
-            int l0 = i0 - h0;
-            if (l0 < 0) l0 += n0;
-            const C v = src[l0];
-            const T sc = s * p0[i0];
-            C o;
-            o.x = v.x * sc;
-            o.y = v.y * sc;
-            dst[i0] = o;
+        // kPerThread modes per thread, consecutive across the lanes of each step
+        for (int b0 = blockIdx.x * blockDim.x * kPerThread; b0 < N0;
+             b0 += gridDim.x * blockDim.x * kPerThread) {
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                const int i0 = b0 + u * (int)blockDim.x + threadIdx.x;
+                if (i0 < N0) {
+                    int l0 = i0 - h0;
+                    if (l0 < 0) l0 += n0;
+                    const C v = src[l0];
+                    const T sc = s * p0[i0];
+                    C o;
+                    o.x = v.x * sc;
+                    o.y = v.y * sc;
+                    dst[i0] = o;
+                }
+            }
         }
     }
 }
@@ -75,25 +85,37 @@ __global__ void precorrect_kernel(const typename cplx<T>::type *__restrict__ f,
             C zero;
             zero.x = 0;
             zero.y = 0;
-            for (int l0 = blockIdx.x * blockDim.x + threadIdx.x; l0 < n0; l0 += gridDim.x * blockDim.x)
-                dst[l0] = zero;
+            for (int b0 = blockIdx.x * blockDim.x * kPerThread; b0 < n0;
+                 b0 += gridDim.x * blockDim.x * kPerThread) {
+#pragma unroll
+                for (int u = 0; u < kPerThread; ++u) {
+                    const int l0 = b0 + u * (int)blockDim.x + threadIdx.x;
+                    if (l0 < n0) dst[l0] = zero;
+                }
+            }
             continue;
         }
         const T s = p1[i1] * p2[i2];
         const C *src = f + (int64_t)tr * Ntot + ((int64_t)i2 * N1 + i1) * N0;
-        for (int l0 = blockIdx.x * blockDim.x + threadIdx.x; l0 < n0; l0 += gridDim.x * blockDim.x) {
-            const int i0 = l0 < c0 ? l0 + h0 : (l0 >= n0 - h0 ? l0 - n0 + h0 : -1);
-            C o;
-            if (i0 >= 0) {
-                const C v = src[i0];
-                const T sc = s * p0[i0];
-                o.x = v.x * sc;
-                o.y = v.y * sc;
-            } else {
-                o.x = 0;
-                o.y = 0;
+        for (int b0 = blockIdx.x * blockDim.x * kPerThread; b0 < n0;
+             b0 += gridDim.x * blockDim.x * kPerThread) {
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                const int l0 = b0 + u * (int)blockDim.x + threadIdx.x;
+                if (l0 >= n0) continue;
+                const int i0 = l0 < c0 ? l0 + h0 : (l0 >= n0 - h0 ? l0 - n0 + h0 : -1);
+                C o;
+                if (i0 >= 0) {
+                    const C v = src[i0];
+                    const T sc = s * p0[i0];
+                    o.x = v.x * sc;
+                    o.y = v.y * sc;
+                } else {
+                    o.x = 0;
+                    o.y = 0;
+                }
+                dst[l0] = o;
             }
-            dst[l0] = o;
         }
     }
 }
@@ -124,9 +146,18 @@ __global__ void correction_kernel(T *__restrict__ out, int N, int n, int w,
     }
 }
 
+// Threads per block for rows of rowlen elements: enough warps to give every
+// thread kPerThread elements, at most 256.
+inline int row_threads(int rowlen)
+{
+    int t = (rowlen + kPerThread - 1) / kPerThread;
+    t = (t + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > 256 ? 256 : t);
+}
+
 inline dim3 row_grid(int64_t rows, int rowlen, int threads)
 {
-    int bx = (rowlen + threads - 1) / threads;
+    int bx = (rowlen + threads * kPerThread - 1) / (threads * kPerThread);
     if (bx < 1) bx = 1;
     int64_t by = rows < 65535 ? rows : 65535;
     return dim3(bx, (unsigned)(by < 1 ? 1 : by), 1);
@@ -136,7 +167,7 @@ template <typename T>
 cudaError_t deconvolve_impl(Plan &p, void *f)
 {
     const int64_t rows = p.N[1] * p.N[2] * p.ntransf;
-    const int threads = 128;
+    const int threads = row_threads((int)p.N[0]);
     count_launch();
     deconvolve_kernel<T><<<row_grid(rows, (int)p.N[0], threads), threads, 0, p.stream>>>(
         reinterpret_cast<const typename cplx<T>::type *>(p.fine),
@@ -150,7 +181,7 @@ template <typename T>
 cudaError_t precorrect_impl(Plan &p, const void *f)
 {
     const int64_t rows = p.nf[1] * p.nf[2] * p.ntransf;
-    const int threads = 128;
+    const int threads = row_threads((int)p.nf[0]);
     count_launch();
     precorrect_kernel<T><<<row_grid(rows, (int)p.nf[0], threads), threads, 0, p.stream>>>(
         reinterpret_cast<const typename cplx<T>::type *>(f),
