@@ -17,7 +17,7 @@
  *   orc_cells          fixed-point bin rule for the bin-sort (Sec. 4.1, GM-sort).
  *   orc_binsort        stable counting sort giving the permutation t (Sec. 4.1).
  *
- * Conventions (readings of the paper, listed in the design doc):
+ * Conventions (readings of the paper where it leaves a choice open):
  *   - complex arrays are interleaved (re, im) doubles;
  *   - mode arrays are [N3][N2][N1] with k1 fastest and k_i running from
  *     -floor(N_i/2) upwards (Eq. "I");

@@ -534,6 +534,9 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
         int64_t mat = cblk > 0 ? p.nbins * cblk : 256 * (int64_t)rblk;
         int64_t L = mat > p.nbins ? mat : p.nbins;
         int64_t parts = scan_parts_needed(L);
+        // the counting sort keeps an int2 of sums per 32 bins there
+        const int64_t groups = 2 * ((p.nbins + 31) / 32);
+        if (parts < groups) parts = groups;
         if (mat > p.mat_cap) {
             dev_free(p.mat);
             p.mat = nullptr;

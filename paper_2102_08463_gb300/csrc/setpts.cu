@@ -7,9 +7,10 @@
 // Two sort paths, both stable and both giving the same t:
 //   counting sort (bins fit in shared memory): each CTA owns a contiguous chunk
 //     of points and histograms its bins in shared memory into row b of a
-//     CTAs x bins matrix; a prefix over the CTAs of each bin plus the scanned
-//     bin totals gives every CTA the first output slot of each of its bins; the
-//     CTA then walks its chunk in order, ranks equal bins inside each tile with
+//     CTAs x bins matrix; a prefix over the CTAs of each bin (which also sums
+//     groups of 32 bins) and one offsets kernel (bin starts from those sums and
+//     a block scan, plus the subproblem list) give every CTA the first output
+//     slot of each of its bins; the CTA then walks its chunk in order, ranks equal bins inside each tile with
 //     __match_any_sync (lanes) and warp order (one barrier per warp), and writes
 //     each point's index into its sorted slot of t.
 //   LSD radix sort (many bins): 8-bit digits, per-CTA digit histograms, a scan
@@ -233,13 +234,15 @@ count_kernel(const T *__restrict__ x, const T *__restrict__ y, const T *__restri
 }
 
 // Counting sort, pass 2: per bin, exclusive prefix over the CTAs (in place) and
-// the bin total.
+// the bin total; per group of 32 bins, the sums of the counts and of the
+// subproblem counts ceil(count / msub) (agg, skipped when null).
 constexpr int kColWarps = 8;
 
 // 32 bins per CTA (lane = bin, coalesced rows); each warp owns a slice of the
 // CTA rows: slice sums, exclusive prefix over slices, then a rescan of the slice.
 __global__ void __launch_bounds__(kColWarps * 32)
-column_scan_kernel(int32_t *__restrict__ mat, int nbins, int nblk, int32_t *__restrict__ bincount)
+column_scan_kernel(int32_t *__restrict__ mat, int nbins, int nblk, int32_t *__restrict__ bincount,
+                   int msub, int2 *__restrict__ agg)
 {
     __shared__ int part[kColWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -256,14 +259,90 @@ column_scan_kernel(int32_t *__restrict__ mat, int nbins, int nblk, int32_t *__re
     __syncthreads();
     int off = 0;
     for (int w = 0; w < warp; ++w) off += part[w][lane];
+    if (warp == kColWarps - 1) {
+        const int cnt = ok ? off + s : 0;
+        if (ok) bincount[b] = cnt;
+        if (agg != nullptr) {
+            int sc = cnt, sn = cnt / msub + (cnt % msub != 0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sc += __shfl_xor_sync(kFull, sc, o);
+                sn += __shfl_xor_sync(kFull, sn, o);
+            }
+            if (lane == 0) agg[blockIdx.x] = make_int2(sc, sn);
+        }
+    }
     if (ok) {
-        if (warp == kColWarps - 1) bincount[b] = off + s;
         for (int r = r0; r < r1; ++r) {
             const int64_t i = (int64_t)r * nbins + b;
             const int v = mat[i];
             mat[i] = off;
             off += v;
         }
+    }
+}
+
+// Counting sort, pass 2b: one thread per bin.  The exclusive prefix of the
+// column-scan groups before the CTA (agg) plus a block scan of (count,
+// subproblems) give each bin its first sorted slot (binstart) and its first
+// subproblem; the bin writes its ceil(count / msub) subproblems (Sec. 4.1 SM
+// step 1) and the last bin the total.
+constexpr int kOffThreads = 256;
+constexpr int kOffGroups = kOffThreads / 32;   // column-scan groups per CTA
+
+__global__ void __launch_bounds__(kOffThreads)
+bin_offsets_kernel(const int32_t *__restrict__ bincount, const int2 *__restrict__ agg, int nbins,
+                   int msub, int32_t *__restrict__ binstart, int4 *__restrict__ subprob,
+                   int32_t *__restrict__ nsub_total)
+{
+    __shared__ int2 red[kOffThreads / 32];
+    __shared__ int2 wtot[kOffThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g0 = blockIdx.x * kOffGroups;
+    const int b = blockIdx.x * kOffThreads + threadIdx.x;
+    const int cnt = b < nbins ? bincount[b] : 0;
+    const int ns = cnt / msub + (cnt % msub != 0);
+    int pc = 0, pn = 0;
+    for (int i = threadIdx.x; i < g0; i += kOffThreads) {
+        const int2 a = agg[i];
+        pc += a.x;
+        pn += a.y;
+    }
+    int ic = cnt, in = ns;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pc += __shfl_xor_sync(kFull, pc, o);
+        pn += __shfl_xor_sync(kFull, pn, o);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int tc = __shfl_up_sync(kFull, ic, o);
+        const int tn = __shfl_up_sync(kFull, in, o);
+        if (lane >= o) {
+            ic += tc;
+            in += tn;
+        }
+    }
+    if (lane == 0) red[warp] = make_int2(pc, pn);
+    if (lane == 31) wtot[warp] = make_int2(ic, in);
+    __syncthreads();
+    int sc = 0, sn = 0;
+#pragma unroll
+    for (int w = 0; w < kOffThreads / 32; ++w) {
+        sc += red[w].x;
+        sn += red[w].y;
+        if (w < warp) {
+            sc += wtot[w].x;
+            sn += wtot[w].y;
+        }
+    }
+    if (b < nbins) {
+        const int start = sc + ic - cnt;
+        const int first = sn + in - ns;
+        binstart[b] = start;
+        for (int k = 0; k < ns; ++k)
+            subprob[first + k] = make_int4(b, start + k * msub, min(msub, cnt - k * msub), 0);
+        if (b == nbins - 1) *nsub_total = first + ns;
     }
 }
 
@@ -284,6 +363,7 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int32_t *col = mat + (int64_t)blockIdx.x * nbins;
+#pragma unroll 4
     for (int i = threadIdx.x; i < nbins; i += blockDim.x) run[i] = col[i] + binstart[i];
     __syncthreads();
     const int64_t beg = (int64_t)blockIdx.x * chunk;
@@ -436,7 +516,7 @@ __global__ void subs_per_bin_kernel(const int32_t *__restrict__ bincount, int64_
 {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
          b += (int64_t)gridDim.x * blockDim.x)
-        nsubs[b] = (bincount[b] + msub - 1) / msub;
+        nsubs[b] = bincount[b] / msub + (bincount[b] % msub != 0);
 }
 
 __global__ void write_subs_kernel(const int32_t *__restrict__ bincount,
@@ -523,17 +603,17 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
         auto ks = rank_scatter_kernel;
         cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        count_launch(3);
+        int2 *agg = reinterpret_cast<int2 *>(p.scan_part);   // (nbins + 31) / 32 groups
+        count_launch(4);
         kc<<<cblk, kCountThreads, smem, st>>>(x, y, z, M, chunk, n, m, nb, nbins, p.w, p.keys,
                                               p.mat, recs);
-        column_scan_kernel<<<(nbins + 31) / 32, kColWarps * 32, 0, st>>>(p.mat, nbins, cblk, p.bincount);
-        e = launch_scan(p, p.bincount, p.binstart, nbins, nullptr);
-        if (e != cudaSuccess) return e;
+        column_scan_kernel<<<(nbins + 31) / 32, kColWarps * 32, 0, st>>>(p.mat, nbins, cblk,
+                                                                         p.bincount, p.msub, agg);
+        bin_offsets_kernel<<<(nbins + kOffThreads - 1) / kOffThreads, kOffThreads, 0, st>>>(
+            p.bincount, agg, nbins, p.msub, p.binstart, p.subprob, p.nsub);
         ks<<<cblk, kCountThreads, smem, st>>>(M, chunk, nbins, p.keys, p.mat, p.binstart, p.vals);
         p.perm = p.vals;
-        count_launch();
-        subs_per_bin_kernel<<<grid_for(nbins, 256, p.num_sms), 256, 0, st>>>(p.bincount, nbins,
-                                                                           p.msub, p.scan_tmp);
+        return cudaGetLastError();
     } else {
         const int g = grid_for(M, 256, p.num_sms);
         count_launch();
@@ -640,7 +720,8 @@ cudaError_t binsort_into_impl(const BinsortScratch &s, int dim, int64_t M, const
     if (e != cudaSuccess) return e;
     count_launch(3);
     kc<<<s.nblk, kCountThreads, smem, st>>>(x, y, z, M, chunk, n, m, nb, nbins, s.keys, s.mat);
-    column_scan_kernel<<<(nbins + 31) / 32, kColWarps * 32, 0, st>>>(s.mat, nbins, s.nblk, bincount);
+    column_scan_kernel<<<(nbins + 31) / 32, kColWarps * 32, 0, st>>>(s.mat, nbins, s.nblk, bincount,
+                                                                     1, nullptr);
     Plan scan_plan;                 // only scan_part and stream are used by launch_scan
     scan_plan.stream = st;
     scan_plan.scan_part = s.scan_part;

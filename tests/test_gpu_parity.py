@@ -4,7 +4,8 @@ Three bars, each stated where it is used:
   * the bin-sort (permutation t, per-bin counts, subproblem count) is bit-exact;
   * against the oracle's own three-step pipeline at the SAME kernel width the
     only differences are rounding: relative l2 <= 2e-5 in single precision,
-    <= 1e-11 in double (DESIGN.md derives both from the arithmetic);
+    <= 1e-11 in double (a few ulps of the working precision times the
+    conditioning of the sums over w^d kernel values and the FFT);
   * against the exact sums, relative l2 <= 2 eps where the oracle pipeline at
     that width meets eps (the width rule of Sec. 3), else <= oracle error plus
     the rounding allowance.
@@ -81,6 +82,38 @@ def test_binsort_bit_exact(nb, dim, kind, M, prec):
     assert np.array_equal(_host(t).astype(np.int64), t_ref)
     assert np.array_equal(_host(bc).astype(np.int64), counts)
     assert nsub == oracle.subproblems(counts, 1024).shape[0]
+    p.close()
+
+
+# Counting sort with tens of thousands of bins (bin starts and subproblem offsets
+# come from sums over groups of 32 bins, several groups per offsets block): t,
+# counts and subproblem count bit-exact, then the spread through those
+# subproblems against the oracle.
+@pytest.mark.parametrize("dim,N,bins,msub,kind,M", [
+    (2, (700, 650), (8, 8), 64, "mixture", 300007),
+    (2, (700, 650), (8, 8), 64, "cluster", 300007),     # one bin, ~4700 subproblems
+    (2, (1024, 1024), (10, 16), 1024, "rand", 400009),
+    (3, (128, 128, 128), (16, 16, 2), 256, "gauss", 200003),
+])
+def test_binsort_counting_many_bins(nb, dim, N, bins, msub, kind, M):
+    p = _plan(nb, 1, N, 1e-5, 0, method="sm", bins=bins, msub=msub)
+    nf = p.params["nf"][:dim]
+    w, beta = p.params["w"], p.params["beta"]
+    assert p.params["nbins"] > 8 * 1024
+    pts = wl.points(kind, dim, M, 3000 + M, np.float32, n=nf, spread=0.3)
+    c = wl.strengths(M, 3001 + M, np.complex64)
+    p.setpts(*_pts_dev(pts, 0))
+    t, bc, nsub = p.sort()
+    p64 = [q.astype(np.float64) for q in pts]
+    _, counts, t_ref = oracle.binsort(p64, nf, bins)
+    assert counts.size == p.params["nbins"]
+    assert np.array_equal(_host(t).astype(np.int64), t_ref)
+    assert np.array_equal(_host(bc).astype(np.int64), counts)
+    assert nsub == oracle.subproblems(counts, msub).shape[0]
+    nb.spread(p.handle, nb._dptr(_dev(c)))
+    g = _host(p.finegrid())
+    ref = oracle.spread(p64, c.astype(np.complex128), nf, w, beta)
+    assert oracle.rel_l2(g, ref) < TOL_F32
     p.close()
 
 
