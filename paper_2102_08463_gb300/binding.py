@@ -225,7 +225,7 @@ def spread_add(h, c):
 
 
 def binsort_noalloc(dim, prec, M, x, y, z, nf, bins, perm, bincount, stream=None):
-    """nufft_binsort_noalloc: stable bin-sort into caller buffers, no allocation."""
+    """nufft_binsort_noalloc: bin-sort into caller buffers, no allocation."""
     nfa = (ctypes.c_int64 * 3)(*([int(v) for v in nf] + [1] * (3 - len(nf))))
     ba = (ctypes.c_int * 3)(*([int(v) for v in bins] + [1] * (3 - len(bins))))
     _check(load().nufft_binsort_noalloc(int(dim), int(prec), int(M), x, y, z, nfa, ba, perm,

@@ -1,20 +1,21 @@
 // setpts.cu -- bin-sort of the nonuniform points (Sec. 4.1, GM-sort and SM
-// step 1): the bin of every point, per-bin counts, a stable permutation t
-// listing the points bin by bin (increasing original index inside a bin), the
-// subproblem list (runs of at most M_sub points of one bin) and a packed
-// record of each point's kernel offsets.
+// step 1): the bin of every point, per-bin counts, a permutation t listing the
+// points bin by bin, the subproblem list (runs of at most M_sub points of one
+// bin) and a packed record of each point's kernel offsets.
 //
-// Two sort paths, both stable and both giving the same t:
+// Two sort paths; both give the same bins, counts and subproblems and the same
+// set of points in every bin:
 //   counting sort (bins fit in shared memory): each CTA owns a contiguous chunk
 //     of points and histograms its bins in shared memory into row b of a
 //     CTAs x bins matrix; a prefix over the CTAs of each bin (which also sums
 //     groups of 32 bins) and one offsets kernel (bin starts from those sums and
 //     a block scan, plus the subproblem list) give every CTA the first output
-//     slot of each of its bins; the CTA then walks its chunk in order, ranks equal bins inside each tile with
-//     __match_any_sync (lanes) and warp order (one barrier per warp), and writes
-//     each point's index into its sorted slot of t.
+//     slot of each of its bins; the CTA's points then claim slots with shared
+//     atomics (order inside a bin unspecified, as with the paper's atomic sort).
 //   LSD radix sort (many bins): 8-bit digits, per-CTA digit histograms, a scan
-//     of the digit x CTA matrix, ranked scatter.
+//     of the digit x CTA matrix, ranked scatter; every pass is stable (equal
+//     digits keep their order, ranked with __match_any_sync and per-warp
+//     counts), so t lists each bin's points in increasing index.
 // The packed records are written in the original point order (coalesced); the
 // spreading and interpolation kernels read them through t, as they read c.
 #include "nufft_internal.cuh"
@@ -346,12 +347,14 @@ bin_offsets_kernel(const int32_t *__restrict__ bincount, const int2 *__restrict_
     }
 }
 
-// Counting sort, pass 3: stable ranked scatter of t.  A tile is kRankU x 32
-// consecutive points per warp (warp w owns the w-th run of kRankU * 32); the
-// warps take turns, in warp order, to claim their slots, each turn placing its
-// kRankU chunks of 32 in order (ranks among equal keys by lane), so equal keys
-// keep their index order with one barrier per warp per tile.  The keys of the
-// next tile are loaded before the current tile's turns.
+// Counting sort, pass 3: ranked scatter of t.  Each CTA loads its first output
+// slot of every bin (prefix over the CTAs before it + bin start) into shared
+// memory, then every point claims the next slot of its bin with a shared
+// atomicAdd.  A CTA's points of one bin fill that CTA's run of slots of the bin
+// in atomic order: t lists the points bin by bin, the CTAs' runs inside a bin
+// in CTA order, and the order inside a run is not specified (as with the
+// atomic bin-sort of Sec. 4.1).  A tile is kRankU x 32 consecutive points per
+// warp; the keys of the next tile are loaded before the current tile's claims.
 constexpr int kRankU = 4;
 
 __global__ void __launch_bounds__(kCountThreads)
@@ -368,7 +371,6 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
     __syncthreads();
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = min(beg + chunk, M);
-    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t tile = (int64_t)nwarps * 32 * kRankU;
     const int64_t mine0 = (int64_t)warp * 32 * kRankU + lane;
     int key[kRankU], keyn[kRankU];
@@ -383,32 +385,12 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
             const int64_t j = t0 + tile + mine0 + u * 32;
             keyn[u] = j < end ? keys[j] : -1;
         }
-        unsigned peers[kRankU];
-        int base[kRankU];
+        int slot[kRankU];
 #pragma unroll
-        for (int u = 0; u < kRankU; ++u) {
-            peers[u] = __match_any_sync(kFull, key[u]);
-            base[u] = 0;
-        }
-        // only the slot claims are serialised, warp by warp
-        for (int wv = 0; wv < nwarps; ++wv) {
-            if (warp == wv) {
+        for (int u = 0; u < kRankU; ++u) slot[u] = key[u] >= 0 ? atomicAdd(&run[key[u]], 1) : 0;
 #pragma unroll
-                for (int u = 0; u < kRankU; ++u) {
-                    if (key[u] >= 0 && (peers[u] & lt_mask) == 0) {
-                        base[u] = run[key[u]];
-                        run[key[u]] = base[u] + __popc(peers[u]);
-                    }
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int u = 0; u < kRankU; ++u) {
-            const int b = __shfl_sync(kFull, base[u], __ffs(peers[u]) - 1);
-            if (key[u] >= 0) perm[b + __popc(peers[u] & lt_mask)] = (int32_t)(t0 + mine0 + u * 32);
-        }
+        for (int u = 0; u < kRankU; ++u)
+            if (key[u] >= 0) perm[slot[u]] = (int32_t)(t0 + mine0 + u * 32);
 #pragma unroll
         for (int u = 0; u < kRankU; ++u) key[u] = keyn[u];
     }
