@@ -188,7 +188,7 @@ __device__ __forceinline__ typename rec4<T>::type make_record_v(T xv, T yv, T zv
 // (mat[cta * nbins + bin], coalesced).  Four points per thread per round keep
 // several loads in flight.
 // ---------------------------------------------------------------------------
-constexpr int kCountThreads = 512;
+constexpr int kCountThreads = 1024;
 constexpr int kCountUnroll = 4;
 
 template <typename T, int DIM>
@@ -538,15 +538,18 @@ cudaError_t launch_scan(Plan &p, const int32_t *in, int32_t *out, int64_t L, int
 
 int64_t scan_parts_needed(int64_t L) { return (L + kScanSeg - 1) / kScanSeg + 1; }
 
-// Blocks of the counting sort for M points and nbins bins (0 = use the radix path).
+// Blocks of the counting sort for M points and nbins bins (0 = use the radix
+// path): one CTA of kCountThreads per SM, fewer for small M (at least 8192
+// points a CTA).  One full-size CTA per SM keeps the CTAs x bins matrix (written
+// by the count, read and rewritten by the column scan, read by the scatter) and
+// each CTA's per-bin setup small against its chunk of points: measured on 2D
+// 2048^2 with 10 x 16 bins, M = 4.2M, setpts 0.103 ms with two 512-thread CTAs
+// per SM against 0.090 ms with one of 1024.
 int counting_sort_blocks(const Plan &p, int64_t M)
 {
     const size_t smem = (size_t)p.nbins * sizeof(int32_t);
     if (smem > (size_t)p.smem_optin) return 0;
-    int per_sm = (int)((size_t)p.smem_per_sm / (smem + 1024));
-    if (per_sm > 4) per_sm = 4;            // 4 x 512 threads fill an SM
-    if (per_sm < 1) per_sm = 1;
-    int64_t blocks = (int64_t)p.num_sms * per_sm;
+    int64_t blocks = p.num_sms;
     const int64_t by_size = (M + 8191) / 8192;
     if (blocks > by_size) blocks = by_size;
     return (int)(blocks < 1 ? 1 : blocks);
