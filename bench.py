@@ -68,8 +68,8 @@ FP64_PEAK_TFLOPS = 1.25
 TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --metrics, bench command
     # of profiles/launches_2d-1024-rand-eps1e-5.md with -k spread_sweep2|interp_warp2)
-    "spread:2d-1024-rand-eps1e-5:ab8e769fb3eb422e": 443805440,
-    "interp:2d-1024-rand-eps1e-5:ab8e769fb3eb422e": 298646272,
+    "spread:2d-1024-rand-eps1e-5:3c9d77fa383990bc": 443805440,
+    "interp:2d-1024-rand-eps1e-5:3c9d77fa383990bc": 298646272,
 }
 
 

@@ -78,6 +78,11 @@ typedef struct {
     int    use_picker;    /* 1 = with method, bin, msub and threads all automatic, let the
                              installed tile picker (nufft_picker_install) choose them at
                              setpts, after the autotuner's cache; 0 = off */
+    int    unordered_bins; /* 0 = t lists the points of every bin in increasing original
+                             index (unique t; the default); 1 = in the order the sort's
+                             shared-memory atomics claim slots (faster setpts, t may differ
+                             between calls; bins, counts and subproblems unchanged).  Plans
+                             whose bins exceed shared memory sort stably either way. */
 } nufft_opts;
 
 /* Fill opts with the defaults listed above. */
@@ -107,11 +112,10 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
 /*
  * Set the nonuniform points (Sec. 1.1 "setup"; bin-sort of Sec. 4.1).
  * Computes each point's fine-grid cell, bins of m1 x m2 (x m3) cells with x
- * fastest, the permutation t listing points bin by bin (the order inside a
- * bin is not specified when the bins fit the shared-memory counting sort, and
- * may differ between calls; with more bins, the stable radix sort lists them in
- * increasing original index), the subproblem list (runs of at most M_sub
- * points of one bin) and packed per-point kernel offsets.
+ * fastest, the permutation t listing points bin by bin (increasing original
+ * index inside a bin, unless the plan was made with opts.unordered_bins), the
+ * subproblem list (runs of at most M_sub points of one bin) and packed
+ * per-point kernel offsets.
  * M = 0 is allowed.  x, y, z: device arrays of M reals (z NULL in 2D).
  */
 int nufft_setpts(nufft_plan plan, int64_t M, const void *x, const void *y, const void *z);
@@ -225,10 +229,10 @@ int nufft_batch_destroy(nufft_batch batch);
  * allocate device memory (code running inside another allocator's callbacks,
  * real-time or embedded callers with a memory budget fixed at start-up, host
  * paths that must not take the driver's allocation locks).  It computes the
- * bin-sort of nufft_setpts -- the permutation t listing the points bin by bin
- * (the same set of points in every bin; the order inside a bin is not
- * specified) and the number of points per bin -- without calling cudaMalloc,
- * cudaFree or any allocating library routine.
+ * bin-sort of nufft_setpts with default options -- the permutation t listing
+ * the points bin by bin (increasing original index inside a bin) and the
+ * number of points per bin -- without calling cudaMalloc, cudaFree or any
+ * allocating library routine.
  *
  *   dim, prec   2 or 3; 0 = float coordinates, 1 = double.
  *   M           number of points, 0 <= M <= 1048576 (else NUFFT_ERR_SIZE).

@@ -73,6 +73,7 @@ class Opts(ctypes.Structure):
         ("threads", ctypes.c_int),
         ("ctas_per_sm", ctypes.c_int),
         ("use_picker", ctypes.c_int),
+        ("unordered_bins", ctypes.c_int),
     ]
 
 
@@ -225,7 +226,7 @@ def spread_add(h, c):
 
 
 def binsort_noalloc(dim, prec, M, x, y, z, nf, bins, perm, bincount, stream=None):
-    """nufft_binsort_noalloc: bin-sort into caller buffers, no allocation."""
+    """nufft_binsort_noalloc: stable bin-sort into caller buffers, no allocation."""
     nfa = (ctypes.c_int64 * 3)(*([int(v) for v in nf] + [1] * (3 - len(nf))))
     ba = (ctypes.c_int * 3)(*([int(v) for v in bins] + [1] * (3 - len(bins))))
     _check(load().nufft_binsort_noalloc(int(dim), int(prec), int(M), x, y, z, nfa, ba, perm,
@@ -522,7 +523,7 @@ class Plan:
 
     def __init__(self, type_, N, eps, iflag=+1, ntransf=1, prec=-1, method="auto",
                  bins=None, msub=0, upsampfac=2.0, stream=None, threads=0, ctas_per_sm=0,
-                 use_picker=False):
+                 use_picker=False, unordered_bins=False):
         import torch
         self._torch = torch
         self.type = int(type_)
@@ -543,6 +544,7 @@ class Plan:
         o.threads = int(threads)
         o.ctas_per_sm = int(ctas_per_sm)
         o.use_picker = 1 if use_picker else 0
+        o.unordered_bins = 1 if unordered_bins else 0
         self.handle = None
         self.handle = makeplan(self.type, self.dim, self.N, iflag, ntransf, eps, prec, o)
         self.params = get_params(self.handle)

@@ -3,7 +3,7 @@
 // Some callers cannot call cudaMalloc: code that runs while memory is being
 // handed out by another allocator, real-time or embedded callers with a fixed
 // memory budget decided at start-up, and host paths that must not take the
-// driver's allocation locks.  For them this file provides the bin-sort
+// driver's allocation locks.  For them this file provides the stable bin-sort
 // of the points (the permutation t and the per-bin counts) with all of its
 // scratch in one file-scope device array of a fixed size, so a call allocates
 // nothing: the caller passes the points and the two output arrays.

@@ -220,6 +220,7 @@ struct Plan {
     double poly[kMaxW][kPolyTerms] = {};
     bool poly_ok = false;
     bool use_picker = false;       // consult the installed tile picker at setpts
+    bool unordered_bins = false;   // counting-sort scatter in shared-atomic order
 };
 
 // Tile settings of a plan (method, bin sizes, subproblem cap, threads per CTA).

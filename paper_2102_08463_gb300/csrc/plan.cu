@@ -387,6 +387,7 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     p.auto_tiles = o.method == NUFFT_METHOD_AUTO && o.bin[0] == 0 && o.bin[1] == 0 &&
                    o.bin[2] == 0 && o.msub == 0 && o.threads == 0;
     p.use_picker = p.auto_tiles && o.use_picker != 0;
+    p.unordered_bins = o.unordered_bins != 0;
     if (p.method == NUFFT_METHOD_SM) {
         size_t cells = 1;
         for (int d = 0; d < dim; ++d) cells *= (size_t)padded(p.m[d], w);

@@ -1,21 +1,19 @@
 // setpts.cu -- bin-sort of the nonuniform points (Sec. 4.1, GM-sort and SM
 // step 1): the bin of every point, per-bin counts, a permutation t listing the
-// points bin by bin, the subproblem list (runs of at most M_sub points of one
-// bin) and a packed record of each point's kernel offsets.
+// points bin by bin (increasing original index inside a bin, unless the plan
+// asks for shared-atomic order), the subproblem list (runs of at most M_sub
+// points of one bin) and a packed record of each point's kernel offsets.
 //
-// Two sort paths; both give the same bins, counts and subproblems and the same
-// set of points in every bin:
+// Two sort paths, both giving the same t in index order:
 //   counting sort (bins fit in shared memory): each CTA owns a contiguous chunk
 //     of points and histograms its bins in shared memory into row b of a
 //     CTAs x bins matrix; a prefix over the CTAs of each bin (which also sums
 //     groups of 32 bins) and one offsets kernel (bin starts from those sums and
 //     a block scan, plus the subproblem list) give every CTA the first output
-//     slot of each of its bins; the CTA's points then claim slots with shared
-//     atomics (order inside a bin unspecified, as with the paper's atomic sort).
+//     slot of each of its bins; the CTA's points then claim slots in index
+//     order (or, on request, in shared-atomic order).
 //   LSD radix sort (many bins): 8-bit digits, per-CTA digit histograms, a scan
-//     of the digit x CTA matrix, ranked scatter; every pass is stable (equal
-//     digits keep their order, ranked with __match_any_sync and per-warp
-//     counts), so t lists each bin's points in increasing index.
+//     of the digit x CTA matrix, ranked scatter; every pass is stable.
 // The packed records are written in the original point order (coalesced); the
 // spreading and interpolation kernels read them through t, as they read c.
 #include "nufft_internal.cuh"
@@ -349,14 +347,21 @@ bin_offsets_kernel(const int32_t *__restrict__ bincount, const int2 *__restrict_
 
 // Counting sort, pass 3: ranked scatter of t.  Each CTA loads its first output
 // slot of every bin (prefix over the CTAs before it + bin start) into shared
-// memory, then every point claims the next slot of its bin with a shared
-// atomicAdd.  A CTA's points of one bin fill that CTA's run of slots of the bin
-// in atomic order: t lists the points bin by bin, the CTAs' runs inside a bin
-// in CTA order, and the order inside a run is not specified (as with the
-// atomic bin-sort of Sec. 4.1).  A tile is kRankU x 32 consecutive points per
-// warp; the keys of the next tile are loaded before the current tile's claims.
+// memory; its points then claim the next slots of their bins.  A tile is
+// kRankU x 32 consecutive points per warp (warp w owns the w-th run of
+// kRankU * 32); the keys of the next tile are loaded before the current tile's
+// claims.
+//   kOrdered (default): t lists every bin's points in increasing index.  Lanes
+//     of a chunk of 32 with equal keys are grouped with __match_any_sync; one
+//     leader per group claims the group's slots with one shared atomicAdd, and
+//     the lanes take them in lane order.  Chunks claim in order (__syncwarp
+//     between them) and warps take turns in warp order (one barrier per warp
+//     per tile), so equal keys keep their index order.
+//   otherwise: every point claims its own slot with a shared atomicAdd, no
+//     turns; a CTA's points of one bin fill its run of slots in atomic order.
 constexpr int kRankU = 4;
 
+template <bool kOrdered>
 __global__ void __launch_bounds__(kCountThreads)
 rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restrict__ keys,
                     const int32_t *__restrict__ mat, const int32_t *__restrict__ binstart,
@@ -371,6 +376,7 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
     __syncthreads();
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = min(beg + chunk, M);
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t tile = (int64_t)nwarps * 32 * kRankU;
     const int64_t mine0 = (int64_t)warp * 32 * kRankU + lane;
     int key[kRankU], keyn[kRankU];
@@ -385,12 +391,40 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
             const int64_t j = t0 + tile + mine0 + u * 32;
             keyn[u] = j < end ? keys[j] : -1;
         }
-        int slot[kRankU];
+        if (kOrdered) {
+            unsigned peers[kRankU];
+            int base[kRankU];
 #pragma unroll
-        for (int u = 0; u < kRankU; ++u) slot[u] = key[u] >= 0 ? atomicAdd(&run[key[u]], 1) : 0;
+            for (int u = 0; u < kRankU; ++u) {
+                peers[u] = __match_any_sync(kFull, key[u]);
+                base[u] = 0;
+            }
+            for (int wv = 0; wv < nwarps; ++wv) {
+                if (warp == wv) {
 #pragma unroll
-        for (int u = 0; u < kRankU; ++u)
-            if (key[u] >= 0) perm[slot[u]] = (int32_t)(t0 + mine0 + u * 32);
+                    for (int u = 0; u < kRankU; ++u) {
+                        if (key[u] >= 0 && (peers[u] & lt_mask) == 0)
+                            base[u] = atomicAdd(&run[key[u]], __popc(peers[u]));
+                        __syncwarp();
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int u = 0; u < kRankU; ++u) {
+                const int b = __shfl_sync(kFull, base[u], __ffs(peers[u]) - 1);
+                if (key[u] >= 0)
+                    perm[b + __popc(peers[u] & lt_mask)] = (int32_t)(t0 + mine0 + u * 32);
+            }
+        } else {
+            int slot[kRankU];
+#pragma unroll
+            for (int u = 0; u < kRankU; ++u)
+                slot[u] = key[u] >= 0 ? atomicAdd(&run[key[u]], 1) : 0;
+#pragma unroll
+            for (int u = 0; u < kRankU; ++u)
+                if (key[u] >= 0) perm[slot[u]] = (int32_t)(t0 + mine0 + u * 32);
+        }
 #pragma unroll
         for (int u = 0; u < kRankU; ++u) key[u] = keyn[u];
     }
@@ -585,7 +619,7 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
         const int64_t chunk = (M + cblk - 1) / cblk;
         const size_t smem = (size_t)nbins * sizeof(int32_t);
         auto kc = p.dim == 2 ? count_kernel<T, 2> : count_kernel<T, 3>;
-        auto ks = rank_scatter_kernel;
+        auto ks = p.unordered_bins ? rank_scatter_kernel<false> : rank_scatter_kernel<true>;
         cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int2 *agg = reinterpret_cast<int2 *>(p.scan_part);   // (nbins + 31) / 32 groups
@@ -700,7 +734,7 @@ cudaError_t binsort_into_impl(const BinsortScratch &s, int dim, int64_t M, const
     auto kc = dim == 2 ? count_keys_kernel<T, 2> : count_keys_kernel<T, 3>;
     cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(rank_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(rank_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     count_launch(3);
@@ -712,8 +746,8 @@ cudaError_t binsort_into_impl(const BinsortScratch &s, int dim, int64_t M, const
     scan_plan.scan_part = s.scan_part;
     e = launch_scan(scan_plan, bincount, s.binstart, nbins, nullptr);
     if (e != cudaSuccess) return e;
-    rank_scatter_kernel<<<s.nblk, kCountThreads, smem, st>>>(M, chunk, nbins, s.keys, s.mat,
-                                                             s.binstart, perm);
+    rank_scatter_kernel<true><<<s.nblk, kCountThreads, smem, st>>>(M, chunk, nbins, s.keys, s.mat,
+                                                                   s.binstart, perm);
     return cudaGetLastError();
 }
 

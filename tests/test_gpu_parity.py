@@ -1,9 +1,9 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
 
 Three bars, each stated where it is used:
-  * the bin-sort is exact: per-bin counts, subproblem count and the set of
-    points listed in every bin of t (the counting sort's order inside a bin is
-    not specified; the radix sort's is, and is compared element by element);
+  * the bin-sort is bit-exact: permutation t, per-bin counts, subproblem count
+    (plans made with unordered_bins: counts, subproblem count and the points of
+    every bin, whose order inside the bin is then not specified);
   * against the oracle's own three-step pipeline at the SAME kernel width the
     only differences are rounding: relative l2 <= 2e-5 in single precision,
     <= 1e-11 in double (a few ulps of the working precision times the
@@ -64,7 +64,8 @@ def _tol(prec):
 
 def _same_bins(t, counts, t_ref):
     """t lists the same points bin by bin as the oracle's t: sorting t inside
-    each bin (the oracle's bins list increasing indices) gives t_ref."""
+    each bin (the oracle's bins list increasing indices) gives t_ref (plans
+    made with unordered_bins)."""
     t = np.asarray(t).astype(np.int64)
     seg = np.repeat(np.arange(counts.size), counts)
     return t.size == t_ref.size and np.array_equal(t[np.lexsort((t, seg))], t_ref)
@@ -76,11 +77,12 @@ def _same_bins(t, counts, t_ref):
 @pytest.mark.parametrize("dim,kind,M", [(2, "rand", 70001), (2, "cluster", 5000), (3, "rand", 40003),
                                         (3, "gauss", 30011), (2, "rand", 1), (3, "cluster", 777)])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_binsort_matches_oracle(nb, dim, kind, M, prec):
+@pytest.mark.parametrize("unordered", [False, True])
+def test_binsort_bit_exact(nb, dim, kind, M, prec, unordered):
     N = (100, 96) if dim == 2 else (40, 36, 30)
     eps = 1e-5 if prec == 0 else 1e-9
     dt = np.float32 if prec == 0 else np.float64
-    p = _plan(nb, 1, N, eps, prec, method="sm")
+    p = _plan(nb, 1, N, eps, prec, method="sm", unordered_bins=unordered)
     nf = p.params["nf"][:dim]
     pts = wl.points(kind, dim, M, 1000 + M, dt, n=nf)
     pts[0][: min(M, 3)] = np.array([-math.pi, math.pi, np.nextafter(dt(math.pi), dt(4))], dt)[: min(M, 3)]
@@ -90,23 +92,27 @@ def test_binsort_matches_oracle(nb, dim, kind, M, prec):
     bins = p.params["bins"][:dim]
     binidx, counts, t_ref = oracle.binsort([q.astype(np.float64) for q in pts], nf, bins)
     assert np.array_equal(_host(bc).astype(np.int64), counts)
-    assert _same_bins(_host(t), counts, t_ref)
+    if unordered:
+        assert _same_bins(_host(t), counts, t_ref)
+    else:
+        assert np.array_equal(_host(t).astype(np.int64), t_ref)
     assert nsub == oracle.subproblems(counts, 1024).shape[0]
     p.close()
 
 
 # Counting sort with tens of thousands of bins (bin starts and subproblem offsets
-# come from sums over groups of 32 bins, several groups per offsets block): the
-# points of every bin, counts and subproblem count exact, then the spread
-# through those subproblems against the oracle.
+# come from sums over groups of 32 bins, several groups per offsets block): t,
+# counts and subproblem count bit-exact (with unordered_bins: the points of
+# every bin), then the spread through those subproblems against the oracle.
+@pytest.mark.parametrize("unordered", [False, True])
 @pytest.mark.parametrize("dim,N,bins,msub,kind,M", [
     (2, (700, 650), (8, 8), 64, "mixture", 300007),
     (2, (700, 650), (8, 8), 64, "cluster", 300007),     # one bin, ~4700 subproblems
     (2, (1024, 1024), (10, 16), 1024, "rand", 400009),
     (3, (128, 128, 128), (16, 16, 2), 256, "gauss", 200003),
 ])
-def test_binsort_counting_many_bins(nb, dim, N, bins, msub, kind, M):
-    p = _plan(nb, 1, N, 1e-5, 0, method="sm", bins=bins, msub=msub)
+def test_binsort_counting_many_bins(nb, dim, N, bins, msub, kind, M, unordered):
+    p = _plan(nb, 1, N, 1e-5, 0, method="sm", bins=bins, msub=msub, unordered_bins=unordered)
     nf = p.params["nf"][:dim]
     w, beta = p.params["w"], p.params["beta"]
     assert p.params["nbins"] > 8 * 1024
@@ -118,7 +124,10 @@ def test_binsort_counting_many_bins(nb, dim, N, bins, msub, kind, M):
     _, counts, t_ref = oracle.binsort(p64, nf, bins)
     assert counts.size == p.params["nbins"]
     assert np.array_equal(_host(bc).astype(np.int64), counts)
-    assert _same_bins(_host(t), counts, t_ref)
+    if unordered:
+        assert _same_bins(_host(t), counts, t_ref)
+    else:
+        assert np.array_equal(_host(t).astype(np.int64), t_ref)
     assert nsub == oracle.subproblems(counts, msub).shape[0]
     nb.spread(p.handle, nb._dptr(_dev(c)))
     g = _host(p.finegrid())
@@ -129,7 +138,7 @@ def test_binsort_counting_many_bins(nb, dim, N, bins, msub, kind, M):
 
 def test_binsort_many_bins_three_passes(nb):
     # 3D fine grid 128^3 with 4x4x2 bins: 32768 * 2 = 65536 bins -> 16-bit keys, 2 radix passes;
-    # 2x2x2 bins on 160^3 -> 512000 bins -> 3 passes.  Stable passes: t equals the oracle's.
+    # 2x2x2 bins on 160^3 -> 512000 bins -> 3 passes
     for N, bins in (((64, 64, 64), (4, 4, 2)), ((80, 80, 80), (2, 2, 2))):
         p = _plan(nb, 1, N, 1e-2, 0, method="gmsort", bins=bins)
         nf = p.params["nf"][:3]

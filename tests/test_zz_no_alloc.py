@@ -2,9 +2,8 @@
 
 nufft_binsort_noalloc serves callers that cannot allocate device memory: it
 keeps all of its scratch in one fixed array inside the library.  Its results
-must equal what nufft_setpts computes (read back with nufft_get_sort) on
-consecutive calls that reuse that array: the same counts, bit for bit, and the
-same points in every bin (the order inside a bin is not specified).  This file is collected last
+must equal what nufft_setpts computes (read back with nufft_get_sort), bit for
+bit, on consecutive calls that reuse that array.  This file is collected last
 so that a run stopping at the first failure has run every other test first.
 """
 import numpy as np
@@ -68,10 +67,5 @@ def test_noalloc_binsort_matches_setpts_twice():
                            nb._dptr(pts[2]) if dim == 3 else None, nf, bins,
                            nb._dptr(perm), nb._dptr(bincount), stream.cuda_stream)
         torch.cuda.synchronize()
+        assert torch.equal(perm, t_ref)
         assert torch.equal(bincount, bc_ref)
-        counts = bc_ref.cpu().numpy().astype(np.int64)
-        seg = np.repeat(np.arange(counts.size), counts)
-        a = perm.cpu().numpy().astype(np.int64)
-        b = t_ref.cpu().numpy().astype(np.int64)
-        assert np.array_equal(a[np.lexsort((a, seg))], b[np.lexsort((b, seg))])
-        assert np.array_equal(np.sort(a), np.arange(M))
