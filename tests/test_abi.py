@@ -49,6 +49,43 @@ def test_strerror_and_default_opts_without_gpu(lib):
     assert o.method == 0 and o.upsampfac == 2.0 and o.msub == 0
 
 
+def _c_struct(name):
+    """(field, C type, array length) of typedef struct { ... } name; in the header."""
+    with open(os.path.join(ROOT, "include", "nufft_gb300.h")) as fh:
+        text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    out = []
+    for decl in body.split(";"):
+        m = re.match(r"\s*([a-z_ ]+?)\s*(\*?)\s*([a-z_0-9]+)\s*(?:\[(\d+)\])?\s*$", decl)
+        if m:
+            out.append((m.group(3), m.group(1) + m.group(2), int(m.group(4) or 1)))
+    return out
+
+
+@pytest.mark.parametrize("c_name,py_name", [("nufft_opts", "Opts"),
+                                            ("nufft_tune_trial", "TuneTrial")])
+def test_ctypes_structs_mirror_the_header(c_name, py_name):
+    from paper_2102_08463_gb300 import binding
+    ctype = {"int": ctypes.c_int, "double": ctypes.c_double, "void*": ctypes.c_void_p}
+    fields = _c_struct(c_name)
+    py = getattr(binding, py_name)._fields_
+    assert [f[0] for f in fields] == [f[0] for f in py]
+    for (name, ct, n), (_, pt) in zip(fields, py):
+        want = ctype[ct] * n if n > 1 else ctype[ct]
+        assert ctypes.sizeof(pt) == ctypes.sizeof(want) and \
+            getattr(pt, "_type_", pt) == getattr(want, "_type_", want), name
+
+
+def test_default_opts_fill_every_field(lib):
+    from paper_2102_08463_gb300 import binding
+    o = binding.Opts()
+    ctypes.memset(ctypes.byref(o), 0x5a, ctypes.sizeof(o))
+    lib.nufft_default_opts(ctypes.byref(o))
+    assert o.method == 0 and list(o.bin) == [0, 0, 0] and o.msub == 0
+    assert o.upsampfac == 2.0 and not o.stream and o.threads == 0 and o.ctas_per_sm == 0
+    assert o.use_picker == 0 and o.unordered_bins == 0
+
+
 def test_algorithmic_cost_per_point_matches_formulas():
     import bench
     # bytes per point at density 1 (fine grid = M cells): 2D 24/48, 3D 28/56
