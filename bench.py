@@ -187,6 +187,33 @@ def make_inputs(W, seed):
     return pts, c, f
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum over the ranks of a list of floats (the list itself
+    without an initialised process group or at world size 1)."""
+    import torch
+    import torch.distributed as dist
+    vals = [float(v) for v in values]
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return vals
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def choose_form(ms_by_form, device="cpu"):
+    """The step schedule with the smallest slowest-rank time; every rank gets
+    the same answer (ties go to the first listed)."""
+    order = list(ms_by_form)
+    worst = max_over_ranks([ms_by_form[k] for k in order], device)
+    return order[min(range(len(order)), key=lambda i: worst[i])]
+
+
+def replica_value(units_per_rank, world, ms_per_step):
+    """Whole-job throughput of `world` replicas: the units all ranks processed
+    over the slowest rank's time per step."""
+    return units_per_rank * world / (ms_per_step / 1e3)
+
+
 def run_gpu(args, W, rank, world, local_rank):
     import torch
     from paper_2102_08463_gb300 import binding
@@ -267,14 +294,7 @@ def run_gpu(args, W, rank, world, local_rank):
         for fn in forms.values():
             fn()
     torch.cuda.synchronize()
-    pick = {k: sorted(time_form(fn, 5))[2] for k, fn in forms.items()}
-    if world > 1:
-        import torch.distributed as dist
-        order = list(forms)
-        tp = torch.tensor([pick[k] for k in order], dtype=torch.float64, device=dev)
-        dist.all_reduce(tp, op=dist.ReduceOp.MAX)
-        pick = dict(zip(order, tp.tolist()))
-    form = min(pick, key=pick.get)
+    form = choose_form({k: sorted(time_form(fn, 5))[2] for k, fn in forms.items()}, dev)
     step = forms[form]
 
     # ---- timed region: K steps, L2 flushed before each, CUDA events on the stream ----
@@ -303,17 +323,16 @@ def run_gpu(args, W, rank, world, local_rank):
     for k, fn in forms.items():
         if k != form:
             form_ms[k] = sum(time_form(fn, args.steps)) / args.steps
+    form_ms = dict(zip(form_ms, max_over_ranks(list(form_ms.values()), dev)))
     r1.close()
     r2.close()
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    total_ms = max_over_ranks([total_ms], dev)[0]
     if world > 1:
         import torch.distributed as dist
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
         dist.barrier()
-    total_ms = float(t_max.item())
     ms_per_step = total_ms / args.steps
     units = 2 * W["M"] * world
-    value = units / (ms_per_step / 1e3)
+    value = replica_value(2 * W["M"], world, ms_per_step)
 
     # ---- stage breakdown and the kernels' own durations (outside the timed region) ----
     def timed(fn, reps=args.stage_reps):
@@ -469,11 +488,7 @@ def run_gpu(args, W, rank, world, local_rank):
     e2e_diff = {"type1": _rd(hfo, fout), "type2": _rd(hco, cout)}
     q1.close()
     q2.close()
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_t.item())
+    e2e_ms = max_over_ranks([e2e_ms], dev)[0]
 
 
     out = {
