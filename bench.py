@@ -68,8 +68,8 @@ FP64_PEAK_TFLOPS = 1.25
 TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --metrics, bench command
     # of profiles/launches_2d-1024-rand-eps1e-5.md with -k spread_sweep2|interp_warp2)
-    "spread:2d-1024-rand-eps1e-5:3c9d77fa383990bc": 443805440,
-    "interp:2d-1024-rand-eps1e-5:3c9d77fa383990bc": 298646272,
+    "spread:2d-1024-rand-eps1e-5:ef3412d7685dad33": 443805440,
+    "interp:2d-1024-rand-eps1e-5:ef3412d7685dad33": 298646272,
 }
 
 
@@ -821,11 +821,11 @@ def run_picker_bench(args):
 
 
 def run_method_sweep(args):
-    """The paper's method comparison (spreading and interpolation time per point of
-    GM, GM-sort and SM against the fine-grid size, uniform and box-clustered points,
-    densities 0.1, 1, 10), 2D single precision at eps = 1e-5, on this GPU.  Sizes
-    with more than 2^24 points are left out; each time is the median of 5 launches
-    (L2 flushed before each)."""
+    """The paper's method comparison on this GPU: spreading and interpolation time
+    per point for each method (GM, GM-sort, SM), by fine-grid size, for uniform and
+    box-clustered points at densities 0.1, 1 and 10; 2D single precision at
+    eps = 1e-5.  Sizes with more than 2^24 points are left out; each time is the
+    median of 5 launches (L2 flushed before each)."""
     import torch
     from paper_2102_08463_gb300 import binding
 

@@ -94,7 +94,7 @@ def set_num_threads(n: int) -> None:
 # Parameters, Sec. 3
 # ---------------------------------------------------------------------------
 def kernel_width(eps: float, sigma: float = 2.0) -> int:
-    """Kernel width w in fine-grid cells.
+    """Number of fine-grid cells w that one point's kernel covers per axis.
 
     sigma = 2: w = ceil(log10(1/eps)) + 1 (Sec. 3).  Powers of ten map to their
     nominal width (a 1e-10 relative guard absorbs the rounding of 1/eps), so
@@ -157,8 +157,8 @@ def es_kernel(z, beta):
 def phihat(xi, beta: float, nquad: int = 200):
     """Fourier transform of the ES kernel, phihat(xi) = int_{-1}^{1} phi(z) cos(xi z) dz.
 
-    The paper says only that the correction factors are precomputed from
-    samples of the kernel's Fourier transform (Sec. 3.1 step 3).  phi has a
+    Sec. 3.1 step 3 builds the correction factors from values of phihat but
+    leaves open how those values are obtained.  phi has a
     square-root edge at |z| = 1, which slows Gauss-Legendre in z to algebraic
     convergence, so the integral is taken in theta with z = sin(theta):
       phihat(xi) = int_{-pi/2}^{pi/2} exp(beta (cos t - 1)) cos(xi sin t) cos t dt,

@@ -173,7 +173,7 @@ __device__ __forceinline__ void spread_sm_item(const KArgs<T> &a, int sp, int tr
             }
         }
         __syncthreads();
-        // Step 3: add the padded bin back to the fine grid, l = (s + Delta) mod n.
+        // Step 3: accumulate the padded bin into the fine grid, l = (s + Delta) mod n.
         int o0, o1, o2;
         bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
         C *grid = a.grid + (int64_t)tr * a.nftot;
