@@ -39,8 +39,13 @@ if ROOT not in sys.path:
 
 from paper_2102_08463_gb300 import workloads as wl  # noqa: E402
 
-METRIC = "NU points/sec (spread/interp and full exec) at eps=1e-5 fp32"
 UNIT = "points/s"
+
+
+def metric_for(W):
+    """The headline metric's name for a workload (its tolerance and precision)."""
+    return "NU points/sec (spread/interp and full exec) at eps=%g %s" % (
+        W["eps"], "fp32" if W["prec"] == 0 else "fp64")
 
 WORKLOADS = {
     "2d-1024-rand-eps1e-5": dict(dim=2, N=(1024, 1024), M=4194304, eps=1e-5, prec=0, kind="rand"),
@@ -57,10 +62,11 @@ DEFAULT_WORKLOAD = "2d-1024-rand-eps1e-5"
 SEED = wl.BASE_SEED + 1
 
 # Roofline denominators.  HBM: the measured copy bandwidth of this GPU pool
-# (MEASURED_PEAKS.json), else 6800 GB/s.  FP32 / FP64 ALU: 152 SMs x 128 FP32
-# lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s; FP64 1.25 TFLOP/s (GB300 nominal).
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+# (MEASURED_PEAKS.json), else 6800 GB/s.  FP32 ALU: the device's SM count (queried)
+# x 128 FP32 lanes x 2 flop x the maximum SM clock (MEASURED_PEAKS.json, else
+# 2070 MHz).  FP64 ALU: the FMA rate measured on the device by the library's
+# nufft_fma_peak kernel (the FP64 unit count per SM is not published for this GPU).
+FP32_LANES_PER_SM = 128
 
 # DRAM traffic per launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel and workload, with the hash of the
@@ -94,6 +100,52 @@ def _peaks():
         except Exception:
             pass
     return hbm, src
+
+
+def _sm_max_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["sm_max_mhz"]), "measured"
+    except Exception:
+        return 2070.0, "fallback"
+
+
+def alu_peaks(dev):
+    """FP32 (derived) and FP32 / FP64 (measured FMA kernel) peaks in TFLOP/s."""
+    import torch
+    from paper_2102_08463_gb300 import binding
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz, mhz_src = _sm_max_mhz()
+    return {"sm_count": sms, "sm_max_mhz": mhz, "sm_max_mhz_source": mhz_src,
+            "fp32_derived_tflops": round(sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, 2),
+            "fp32_measured_tflops": round(binding.fma_peak(0), 2),
+            "fp64_measured_tflops": round(binding.fma_peak(1), 3)}
+
+
+def roofline_of(W, w, kernel_ms, peaks):
+    """Roofline of one spread / interp launch: the slower of algorithmic bytes at
+    the measured HBM bandwidth and algorithmic flops at the ALU peak."""
+    hbm, hbm_src = _peaks()
+    byts, flops = algorithmic_cost(W, w, "spread")
+    if W["prec"] == 0:
+        fp_peak, fp_src = peaks["fp32_derived_tflops"], "derived: %d SMs x 128 FP32 lanes x 2 x %g MHz" % (
+            peaks["sm_count"], peaks["sm_max_mhz"])
+    else:
+        fp_peak, fp_src = peaks["fp64_measured_tflops"], "measured: nufft_fma_peak FP64 kernel"
+    t = kernel_ms / 1e3
+    if byts / (hbm * 1e9) >= flops / (fp_peak * 1e12):
+        ach = byts / t / 1e9
+        r = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+             "frac": round(ach / hbm, 4), "peak_source": hbm_src}
+    else:
+        ach = flops / t / 1e12
+        r = {"bound": "alu", "achieved": round(ach, 3), "peak": fp_peak, "unit": "TFLOP/s",
+             "frac": round(ach / fp_peak, 4), "peak_source": fp_src}
+    r["algorithmic_bytes"] = byts
+    r["algorithmic_flops"] = flops
+    r["kernel_ms"] = round(kernel_ms, 5)
+    return r
 
 
 def algorithmic_cost(W, w, kernel):
@@ -369,26 +421,9 @@ def run_gpu(args, W, rank, world, local_rank):
     torch.cuda.synchronize()
 
     # ---- roofline of the dominant kernel ----
-    hbm, hbm_src = _peaks()
-    byts, flops = algorithmic_cost(W, w, "spread")
-    fp_peak = FP32_PEAK_TFLOPS if W["prec"] == 0 else FP64_PEAK_TFLOPS
-    roof = {}
-    for name, key in (("spread", "spread_ms"), ("interp", "interp_ms")):
-        t = stages[key] / 1e3
-        t_hbm = byts / (hbm * 1e9)
-        t_alu = flops / (fp_peak * 1e12)
-        if t_hbm >= t_alu:
-            ach = byts / t / 1e9
-            roof[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                          "frac": round(ach / hbm, 4), "peak_source": hbm_src}
-        else:
-            ach = flops / t / 1e12
-            roof[name] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp_peak, 2),
-                          "unit": "TFLOP/s", "frac": round(ach / fp_peak, 4),
-                          "peak_source": "derived: SM count x lanes x 2 x max clock"}
-        roof[name]["algorithmic_bytes"] = byts
-        roof[name]["algorithmic_flops"] = flops
-        roof[name]["kernel_ms"] = round(stages[key], 5)
+    peaks = alu_peaks(dev)
+    roof = {name: roofline_of(W, w, stages[key], peaks)
+            for name, key in (("spread", "spread_ms"), ("interp", "interp_ms"))}
     dom = "spread" if stages["spread_ms"] >= stages["interp_ms"] else "interp"
     roofline = dict(roof[dom])
     roofline["kernel"] = dom
@@ -492,7 +527,7 @@ def run_gpu(args, W, rank, world, local_rank):
 
 
     out = {
-        "metric": METRIC,
+        "metric": metric_for(W),
         "value": round(value, 1),
         "unit": UNIT,
         "n_gpus": world,
@@ -517,6 +552,7 @@ def run_gpu(args, W, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
         "roofline_kernels": roof,
+        "alu_peaks": peaks,
         "stages_ms": {k: round(v, 5) for k, v in stages.items()},
         "pts_per_s": {
             "spread": round(W["M"] / (stages["spread_ms"] / 1e3), 1),
@@ -540,6 +576,78 @@ def run_gpu(args, W, rank, world, local_rank):
     p1.close()
     p2.close()
     return out
+
+
+CONFIG_ROWS = ("3d-128-rand-eps1e-6", "2d-1024-rand-eps1e-9", "2d-64-rand-eps1e-5")
+
+
+def measure_config(name, reps=5, nsamp=32):
+    """One more workload measured beside the headline: setpts, spread, interp and
+    both executes (median of `reps`, L2 flushed before each), the roofline of
+    spreading and interpolation, and the relative l2 error of both types against
+    the exact sums on `nsamp` sampled modes / targets."""
+    import torch
+    from paper_2102_08463_gb300 import binding
+
+    W = dict(WORKLOADS[name])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    p1 = binding.Plan(1, W["N"], W["eps"], prec=W["prec"], stream=stream)
+    p2 = binding.Plan(2, W["N"], W["eps"], prec=W["prec"], stream=stream)
+    W["nf"] = p1.params["nf"][: W["dim"]]
+    w = p1.params["w"]
+    pts, c, f = make_inputs(W, SEED + 29)
+    dpts = [torch.from_numpy(p).to(dev) for p in pts]
+    dc = torch.from_numpy(c).to(dev)
+    df = torch.from_numpy(f).to(dev)
+    fout = torch.empty(tuple(reversed(W["N"])), dtype=p1.complex_dtype, device=dev)
+    cout = torch.empty(W["M"], dtype=p1.complex_dtype, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    p1.setpts(*dpts)
+    p2.setpts(*dpts)
+
+    def med(fn):
+        ts = []
+        for _ in range(reps + 1):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ts = sorted(ts[1:])
+        return ts[len(ts) // 2]
+
+    h1, h2 = p1.handle, p2.handle
+    st = {"setpts_ms": med(lambda: p1.setpts(*dpts)),
+          "spread_ms": med(lambda: binding.spread_add(h1, binding._dptr(dc))),
+          "interp_ms": med(lambda: binding.interp(h2, binding._dptr(cout))),
+          "exec_type1_ms": med(lambda: binding.execute(h1, binding._dptr(dc), binding._dptr(fout))),
+          "exec_type2_ms": med(lambda: binding.execute(h2, binding._dptr(cout), binding._dptr(df)))}
+    peaks = alu_peaks(dev)
+    p1.execute(c=dc, f=fout)
+    p2.execute(f=df, c=cout)
+    torch.cuda.synchronize()
+    acc = sampled_accuracy(W, pts, c, f, fout.cpu().numpy(), cout.cpu().numpy(), nsamp=nsamp)
+    p1.close()
+    p2.close()
+    M = W["M"]
+    return {
+        "workload": "%dD type 1 + type 2, N=%s, fine grid %s, M=%d, eps=%g, %s, %s points"
+                    % (W["dim"], "x".join(map(str, W["N"])), "x".join(map(str, W["nf"])), M,
+                       W["eps"], "complex64" if W["prec"] == 0 else "complex128", W["kind"]),
+        "kernel_width": w,
+        "stages_ms": {k: round(v, 5) for k, v in st.items()},
+        "pts_per_s": {"spread": round(M / (st["spread_ms"] / 1e3), 1),
+                      "interp": round(M / (st["interp_ms"] / 1e3), 1),
+                      "exec_type1": round(M / (st["exec_type1_ms"] / 1e3), 1),
+                      "exec_type2": round(M / (st["exec_type2_ms"] / 1e3), 1)},
+        "roofline": {"spread": roofline_of(W, w, st["spread_ms"], peaks),
+                     "interp": roofline_of(W, w, st["interp_ms"], peaks)},
+        "rel_l2_vs_exact": acc,
+    }
 
 
 def sampled_accuracy(W, pts, c, f, f_gpu, c_gpu, nsamp=48):
@@ -589,6 +697,26 @@ def cpu_sample(W, budget_s):
     return m
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def run_cpu_baseline(W, budget_s=15.0, steps=1, gpu_outputs=None):
     """The oracle timed on the host cores; with the GPU arm's outputs, also the
     relative l2 error of those outputs on sampled modes / targets against the
@@ -603,11 +731,23 @@ def run_cpu_baseline(W, budget_s=15.0, steps=1, gpu_outputs=None):
     for _ in range(steps):
         oracle_step(Ws, pts, c, f)
     dt = (time.perf_counter() - t0) / steps
+    # the same step on one thread, on a quarter of the sample
+    m1 = max(1, m // 4)
+    W1 = dict(W, M=m1)
+    pts1, c1, f1 = make_inputs(W1, SEED)
+    oracle.set_num_threads(1)
+    t0 = time.perf_counter()
+    oracle_step(W1, pts1, c1, f1)
+    dt1 = time.perf_counter() - t0
+    oracle.set_num_threads(cores)
     out = {"value": round(2 * m / dt, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "cpu_model": cpu_model(),
            "sample": "one type 1 + type 2 FP64 oracle pipeline step (C spread/interp with "
                      "OpenMP, numpy FFT) on %d of the %d points, full %s fine grid, eps=%g"
                      % (m, W["M"], "x".join(map(str, W["nf"])), W["eps"]),
-           "s_per_step": round(dt, 3)}
+           "s_per_step": round(dt, 3),
+           "one_thread": {"value": round(2 * m1 / dt1, 1), "unit": UNIT, "points": m1,
+                          "s_per_step": round(dt1, 3)}}
     if gpu_outputs is not None:
         out["gpu_rel_l2_sampled"] = sampled_accuracy(W, *gpu_outputs)
     return out
@@ -633,7 +773,7 @@ def run_reference(args, W, rank):
     value = 2 * m / dt
     return {
         "impl": "reference",
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+        "metric": metric_for(W), "value": round(value, 1), "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64",
@@ -904,6 +1044,8 @@ def main():
     ap.add_argument("--stage-reps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the sampled accuracy check")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the extra workloads measured beside the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -938,6 +1080,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = run_cpu_baseline(
             W, gpu_outputs=None if args.no_accuracy else outputs)
+    if rank == 0 and world == 1 and not args.no_configs:
+        # the other spec rows, measured in the same run (outside the timed region)
+        out["configs"] = {name: measure_config(name) for name in CONFIG_ROWS
+                          if name != args.workload}
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

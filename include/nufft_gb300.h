@@ -52,7 +52,7 @@ extern "C" {
 #define NUFFT_ERR_CUDA        -5   /* CUDA runtime error while enqueueing work */
 #define NUFFT_ERR_CUFFT       -6   /* cuFFT plan or execution error */
 #define NUFFT_ERR_NOPTS       -7   /* execute before setpts */
-#define NUFFT_ERR_TIMEOUT     -8   /* a bounded device wait gave up (batched launch) */
+#define NUFFT_ERR_CHECK       -8   /* a device-side check of opts.debug_checks failed */
 #define NUFFT_ERR_METHOD      -9   /* requested method not available for this plan */
 
 /* Spreading / interpolation methods (Sec. 4.1, 4.2). */
@@ -83,6 +83,10 @@ typedef struct {
                              shared-memory atomics claim slots (faster setpts, t may differ
                              between calls; bins, counts and subproblems unchanged).  Plans
                              whose bins exceed shared memory sort stably either way. */
+    int    debug_checks;  /* 1 = setpts also checks on the device that every coordinate is
+                             finite and inside [-3 pi, 3 pi] and that t is a permutation,
+                             and records a failure in a device status word instead of
+                             trapping; nufft_get_status reads it.  0 = off (the default). */
 } nufft_opts;
 
 /* Fill opts with the defaults listed above. */
@@ -127,6 +131,24 @@ int nufft_setpts(nufft_plan plan, int64_t M, const void *x, const void *y, const
  */
 int nufft_execute(nufft_plan plan, void *c, void *f);
 
+/*
+ * Set points and execute from HOST memory ("total+mem" of Sec. 5: the timing
+ * that includes the host-device transfers).  x, y, z (M reals each), c
+ * (ntransf*M complex) and f (ntransf*N complex) are host arrays with the same
+ * layouts and roles as in nufft_setpts / nufft_execute: type 1 reads c and
+ * writes f, type 2 reads f and writes c.  On the plan's stream the points are
+ * copied in and sorted while the input array is copied on an internal stream;
+ * the execute waits for that copy, then the output is copied back.  The call is
+ * asynchronous: the output is valid, and the host arrays may be reused, once the
+ * plan's stream has passed the call.  Page-locked (pinned) host arrays let the
+ * copies overlap the kernels; pageable arrays work but their copies are staged
+ * synchronously by the CUDA runtime.  Device staging for the points, c and f is
+ * allocated on first use (and when M grows) and held by the plan.
+ * Errors as nufft_setpts / nufft_execute (NUFFT_ERR_ALLOC for the staging).
+ */
+int nufft_execute_host(nufft_plan plan, int64_t M, const void *x, const void *y, const void *z,
+                       void *c, void *f);
+
 /* Free everything the plan owns (Sec. 1.1 "destroy").  NULL is accepted. */
 int nufft_destroy(nufft_plan plan);
 
@@ -164,9 +186,35 @@ int nufft_get_sort(nufft_plan plan, int32_t *t, int32_t *bincounts, int32_t *nsu
    threads of *out and leaves the other fields alone. */
 int nufft_get_tiles(nufft_plan plan, nufft_opts *out);
 
+/* Result of the device-side checks of a plan made with opts.debug_checks = 1:
+   waits for the plan's stream, then returns NUFFT_OK if every setpts since the
+   plan was made (or since the last call) passed, NUFFT_ERR_CHECK if one did not
+   (a coordinate NaN, infinite or outside [-3 pi, 3 pi], or t not a permutation),
+   and clears the status.  Plans without debug_checks return NUFFT_OK. */
+int nufft_get_status(nufft_plan plan);
+
+/* ---- fault injection, for tests of the error paths (host side only) ----
+ * nufft_debug_fail(kind, after) arms a process-wide failure: the (after + 1)-th
+ * next device allocation made by this library (kind NUFFT_FAIL_ALLOC) or cuFFT
+ * plan creation (NUFFT_FAIL_CUFFT) fails as an out-of-memory or cuFFT error would,
+ * without touching the device; after < 0 disarms.  Returns the number of
+ * allocations (or cuFFT plans) made since the last call, so a test can count the
+ * failure points of an entry point.  Not part of the transform. */
+#define NUFFT_FAIL_ALLOC 1
+#define NUFFT_FAIL_CUFFT 2
+int nufft_debug_fail(int kind, int after);
+
 /* Number of CUDA kernels this library has launched in this process (all plans,
    all threads).  cuFFT's own kernels are not counted. */
 uint64_t nufft_get_launch_count(void);
+
+/* Measured FMA throughput of the current device in TFLOP/s (an FMA counts as two
+   operations): a kernel of independent FMA chains over all SMs, timed with CUDA
+   events on stream (NULL = legacy default stream); prec 0 = float, 1 = double.
+   The benchmark's roofline denominator for arithmetic-bound kernels; not part of
+   the transform (the paper has no counterpart).  Synchronizes stream.
+   Errors: NUFFT_ERR_ARG, NUFFT_ERR_CUDA. */
+int nufft_fma_peak(int prec, double *tflops, void *stream);
 
 /* ---- autotuner ----
  * The paper hand-tunes its tiles for its own GPU (Sec. 4.1 remark).  This times
@@ -203,19 +251,24 @@ int nufft_tune_cache_clear(void);
 /* ---- batched execution of many plans ----
  * Not in the paper (its interface runs one plan at a time); for workloads of
  * many independent transforms of uneven N and M.  Plans that share type,
- * dimension, precision, kernel width and method (SM or GM-sort) are grouped, and
- * each group's spreading / interpolation runs as one persistent launch over the
- * subproblems of all its plans; clears, corrections and cuFFT stay per plan.
+ * dimension, precision, kernel width and method are grouped, and each group's
+ * spreading / interpolation runs as one persistent launch over the subproblems
+ * (GM: chunks of points) of all its plans; clears, corrections and cuFFT stay
+ * per plan.
  *
  * nufft_batch_create: plans[0..nplans) must be distinct and set up (setpts)
  *   before each execute; while the batch exists they run on `stream` (their cuFFT
  *   plans are re-bound to it) and must not be used on their own.  Destroying the
  *   batch hands them back their own streams.
- * nufft_batch_execute: c[k], f[k] are the plan-k arrays of nufft_execute.
+ * nufft_batch_execute: c[k], f[k] are the plan-k arrays of nufft_execute.  Calls
+ *   may follow one another without a host synchronization; each call's arguments
+ *   are staged in host buffers of their own until its copies have run.
  * nufft_batch_capture: records the execute of these c / f arrays into a CUDA
  *   graph (stream must not be NULL); nufft_batch_launch replays it.  Re-running
  *   setpts on a member with the same M keeps the graph valid; a larger M or a new
- *   subproblem capacity reallocates and needs a new capture.
+ *   subproblem capacity reallocates and needs a new capture.  The graph keeps the
+ *   arguments of its capture: later nufft_batch_execute calls with other arrays
+ *   do not change what it replays.  Capturing waits for the stream to drain.
  * Errors as nufft_execute; NUFFT_ERR_NOPTS from launch when nothing was captured. */
 typedef struct nufft_batch_s *nufft_batch;
 int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_batch *out);
@@ -245,12 +298,17 @@ int nufft_batch_destroy(nufft_batch batch);
  *   stream      cudaStream_t (NULL = legacy default stream); asynchronous.
  * Scratch: one fixed device array of about 8.1 MB inside the library, resident
  * on every device that loads it until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make the
- * first call on each device before any stream capture.  Every call overwrites
- * all scratch it uses, but all calls on a device share the one array: calls
- * whose GPU work could overlap (other streams, other host threads) race and must
- * be serialised by the caller.  Errors: NUFFT_ERR_ARG, NUFFT_ERR_SIZE,
- * NUFFT_ERR_CUDA; nothing is written on an argument error. */
+ * device looks up that array's device address (cudaGetSymbolAddress) and raises
+ * the kernels' shared-memory limits; with CUDA's lazy module loading (the
+ * default) that first call, or the library's first kernel use on the device, is
+ * also when the driver loads the module and places the array, which may
+ * allocate device memory.  Callers that must not allocate later should make one
+ * call per device at start-up (M = 0 is enough) and before any stream capture;
+ * later calls allocate nothing.  Every call overwrites all scratch it uses, but
+ * all calls on a device share the one array: calls whose GPU work could overlap
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Errors: NUFFT_ERR_ARG, NUFFT_ERR_SIZE, NUFFT_ERR_CUDA; nothing is
+ * written on an argument error. */
 int nufft_binsort_noalloc(int dim, int prec, int64_t M, const void *x, const void *y,
                           const void *z, const int64_t *nf, const int *bins, int32_t *perm,
                           int32_t *bincount, void *stream);

@@ -21,7 +21,8 @@ NUFFT_ERR_ALLOC = -4
 NUFFT_ERR_CUDA = -5
 NUFFT_ERR_CUFFT = -6
 NUFFT_ERR_NOPTS = -7
-NUFFT_ERR_TIMEOUT = -8
+NUFFT_ERR_CHECK = -8
+FAIL_ALLOC, FAIL_CUFFT = 1, 2
 NUFFT_ERR_METHOD = -9
 
 METHOD_AUTO, METHOD_GM, METHOD_GM_SORT, METHOD_SM = 0, 1, 2, 3
@@ -39,7 +40,8 @@ EXPORTS = (
     "nufft_picker_set_params", "nufft_picker_get_params", "nufft_picker_save",
     "nufft_picker_load", "nufft_picker_predict", "nufft_picker_grad", "nufft_picker_step",
     "nufft_picker_train", "nufft_picker_loss", "nufft_picker_install", "nufft_picker_features",
-    "nufft_point_skew",
+    "nufft_point_skew", "nufft_fma_peak", "nufft_execute_host", "nufft_get_status",
+    "nufft_debug_fail",
 )
 
 PICKER_NFEAT = 12
@@ -74,6 +76,7 @@ class Opts(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int),
         ("use_picker", ctypes.c_int),
         ("unordered_bins", ctypes.c_int),
+        ("debug_checks", ctypes.c_int),
     ]
 
 
@@ -153,6 +156,10 @@ def load():
                                               ctypes.c_double, I64, ctypes.c_double,
                                               ctypes.POINTER(Opts), FP]
         lib.nufft_point_skew.argtypes = [I, I, I64, P, P, P, ctypes.POINTER(ctypes.c_double), P]
+        lib.nufft_fma_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double), P]
+        lib.nufft_execute_host.argtypes = [P, I64, P, P, P, P, P]
+        lib.nufft_get_status.argtypes = [P]
+        lib.nufft_debug_fail.argtypes = [I, I]
         for name in EXPORTS:
             if name not in ("nufft_default_opts", "nufft_strerror", "nufft_get_launch_count"):
                 getattr(lib, name).restype = I
@@ -189,6 +196,19 @@ def _dptr(t, dtype=None, what="array"):
         raise ValueError("%s must be contiguous" % what)
     if dtype is not None and t.dtype != dtype:
         raise TypeError("%s has dtype %s, expected %s" % (what, t.dtype, dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(t, dtype=None, what="array"):
+    """Raw pointer of a contiguous host (CPU) tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise ValueError("%s must be a host tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (what, dtype, t.dtype))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -467,6 +487,27 @@ def get_launch_count() -> int:
     return int(load().nufft_get_launch_count())
 
 
+def get_status(h):
+    """nufft_get_status: raises NufftError(NUFFT_ERR_CHECK) if a device-side check failed."""
+    _check(load().nufft_get_status(h), "nufft_get_status")
+
+
+def debug_fail(kind, after):
+    """nufft_debug_fail: arm (after >= 0) or disarm a host-side injected failure;
+    returns the number of allocations / cuFFT plans made since the last call."""
+    rc = load().nufft_debug_fail(int(kind), int(after))
+    if rc < 0:
+        raise NufftError(rc, "nufft_debug_fail")
+    return rc
+
+
+def fma_peak(prec=0, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (prec 0 float, 1 double)."""
+    v = ctypes.c_double(0.0)
+    _check(load().nufft_fma_peak(int(prec), ctypes.byref(v), stream), "nufft_fma_peak")
+    return float(v.value)
+
+
 def interp(h, c):
     _check(load().nufft_interp(ctypes.c_void_p(h), c), "nufft_interp")
 
@@ -523,7 +564,7 @@ class Plan:
 
     def __init__(self, type_, N, eps, iflag=+1, ntransf=1, prec=-1, method="auto",
                  bins=None, msub=0, upsampfac=2.0, stream=None, threads=0, ctas_per_sm=0,
-                 use_picker=False, unordered_bins=False):
+                 use_picker=False, unordered_bins=False, debug_checks=False):
         import torch
         self._torch = torch
         self.type = int(type_)
@@ -545,6 +586,7 @@ class Plan:
         o.ctas_per_sm = int(ctas_per_sm)
         o.use_picker = 1 if use_picker else 0
         o.unordered_bins = 1 if unordered_bins else 0
+        o.debug_checks = 1 if debug_checks else 0
         self.handle = None
         self.handle = makeplan(self.type, self.dim, self.N, iflag, ntransf, eps, prec, o)
         self.params = get_params(self.handle)
@@ -580,6 +622,34 @@ class Plan:
             c = torch.empty(shp_c, dtype=cd, device=dev)
         execute(self.handle, _dptr(c, cd, "c"), _dptr(f, cd, "f"))
         return c
+
+    def execute_host(self, x, y, z=None, c=None, f=None, sync=True):
+        """nufft_execute_host on host (CPU) tensors: set the points and execute with
+        the copies inside the call.  Type 1 reads c and returns f (new, or into f);
+        type 2 reads f and returns c.  Pinned tensors let the copies overlap the
+        kernels.  With sync=True the plan's stream is synchronised before returning."""
+        torch = self._torch
+        rd, cd = self.real_dtype, self.complex_dtype
+        M = x.shape[0]
+        shp_f = tuple(reversed(self.N))
+        shp_c = (M,)
+        if self.ntransf > 1:
+            shp_f = (self.ntransf,) + shp_f
+            shp_c = (self.ntransf,) + shp_c
+        pin = bool(x.is_pinned())
+        if self.type == 1:
+            if f is None:
+                f = torch.empty(shp_f, dtype=cd, pin_memory=pin)
+        elif c is None:
+            c = torch.empty(shp_c, dtype=cd, pin_memory=pin)
+        args = [_hptr(x, rd, "x"), _hptr(y, rd, "y"), _hptr(z, rd, "z") if self.dim == 3 else None,
+                _hptr(c, cd, "c"), _hptr(f, cd, "f")]
+        _check(load().nufft_execute_host(self.handle, M, *args), "nufft_execute_host")
+        self.M = M
+        self._pts = (x, y, z, c, f)   # keep alive until the stream has consumed them
+        if sync:
+            self.stream.synchronize()
+        return f if self.type == 1 else c
 
     def finegrid(self):
         """Copy of the plan's fine grid as a complex tensor ([ntransf,] n3, n2, n1).

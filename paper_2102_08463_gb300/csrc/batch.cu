@@ -2,11 +2,12 @@
 // transforms of uneven N and M; not in the paper, whose interface runs one plan
 // at a time).
 //
-// Plans that share type, dimension, precision, kernel width and method (SM or
-// GM-sort) form a group; each group's spreading or interpolation runs as ONE
-// persistent launch over the work items of all its plans ((plan, subproblem,
-// transform) triples, located by a binary search over device-side work offsets
-// computed from each plan's subproblem count).  The fine-grid clear, the
+// Plans that share type, dimension, precision, kernel width and method form a
+// group; each group's spreading or interpolation runs as ONE persistent launch
+// over the work items of all its plans ((plan, subproblem, transform) triples,
+// or (plan, chunk of kGmChunk points, transform) for GM plans, located by a
+// binary search over device-side work offsets computed from each plan's
+// subproblem or chunk count).  The fine-grid clear, the
 // correction steps and cuFFT stay one call per plan.  The whole sequence can be
 // captured once into a CUDA graph and replayed with one launch.
 #include <algorithm>
@@ -32,6 +33,14 @@ __global__ void batch_workoff_kernel(const int32_t *const *__restrict__ nsub,
     workoff[nplans] = s;
 }
 
+// Host staging of the kernel arguments: a direct execute fills the next of
+// kRing pinned slots, after waiting for the event that marks the end of that
+// slot's previous copy, so back-to-back executes never overwrite arguments that
+// an earlier copy has yet to read.  A captured graph copies from a slot of its
+// own (graph_h_args) into a device array of its own (graph_d_args), written
+// only when the graph is captured; executes never touch either.
+constexpr int kRing = 4;
+
 struct Group {
     int type = 1, dim = 2, prec = 0, w = 0, method = NUFFT_METHOD_SM;
     int variant = 0;                   // row-sweep form (sweep_variant), part of the key
@@ -39,8 +48,12 @@ struct Group {
     std::vector<int> members;          // indices into the batch's plans
     size_t smem = 0;                   // max padded-bin bytes over the members
     size_t args_bytes = 0;             // one KArgs<T> per member
-    void *d_args = nullptr;            // device KArgs array
-    void *h_args = nullptr;            // pinned staging for the KArgs array
+    void *d_args = nullptr;            // device KArgs array (direct executes)
+    void *h_ring[kRing] = {};          // pinned staging slots (direct executes)
+    cudaEvent_t ev_ring[kRing] = {};   // end of each slot's last copy
+    int ring_next = 0;
+    void *graph_d_args = nullptr;      // device KArgs array read by the captured graph
+    void *graph_h_args = nullptr;      // pinned source of the graph's copy
     int64_t *d_workoff = nullptr;      // device [members + 1]
     const int32_t **d_nsub = nullptr;  // device array of the members' nsub pointers
     int *d_ntransf = nullptr;
@@ -48,15 +61,10 @@ struct Group {
 
 size_t real_bytes(int prec) { return prec == 0 ? 4 : 8; }
 
-bool groupable(const Plan &p)
-{
-    return p.method == NUFFT_METHOD_SM || p.method == NUFFT_METHOD_GM_SORT;
-}
-
 template <typename T>
-void fill_args(const std::vector<nufft_plan> &plans, const Group &g, void *const *c)
+void fill_args(const std::vector<nufft_plan> &plans, const Group &g, void *const *c, void *host)
 {
-    KArgs<T> *dst = reinterpret_cast<KArgs<T> *>(g.h_args);
+    KArgs<T> *dst = reinterpret_cast<KArgs<T> *>(host);
     for (size_t i = 0; i < g.members.size(); ++i) {
         const int k = g.members[i];
         const Plan &p = plans[k]->p;
@@ -93,7 +101,6 @@ struct nufft_batch_s {
     std::vector<nufft_plan> plans;
     std::vector<cudaStream_t> saved_streams;
     std::vector<Group> groups;
-    std::vector<int> singles;          // plans executed one by one (GM)
     cudaStream_t stream = nullptr;
     int num_sms = 152;
     cudaGraph_t graph = nullptr;
@@ -108,7 +115,12 @@ void free_batch(nufft_batch_s *b)
     if (b->graph) cudaGraphDestroy(b->graph);
     for (Group &g : b->groups) {
         if (g.d_args) cudaFree(g.d_args);
-        if (g.h_args) cudaFreeHost(g.h_args);
+        for (int i = 0; i < kRing; ++i) {
+            if (g.h_ring[i]) cudaFreeHost(g.h_ring[i]);
+            if (g.ev_ring[i]) cudaEventDestroy(g.ev_ring[i]);
+        }
+        if (g.graph_d_args) cudaFree(g.graph_d_args);
+        if (g.graph_h_args) cudaFreeHost(g.graph_h_args);
         if (g.d_workoff) cudaFree(g.d_workoff);
         if (g.d_nsub) cudaFree(g.d_nsub);
         if (g.d_ntransf) cudaFree(g.d_ntransf);
@@ -122,7 +134,9 @@ void free_batch(nufft_batch_s *b)
     delete b;
 }
 
-int run_batch(nufft_batch_s *b, void *const *c, void *const *f)
+// One batched execute.  for_graph: the call is being captured; the arguments
+// go through the graph's own staging (see kRing).
+int run_batch(nufft_batch_s *b, void *const *c, void *const *f, bool for_graph)
 {
     cudaStream_t st = b->stream;
     for (size_t k = 0; k < b->plans.size(); ++k) {
@@ -146,15 +160,29 @@ int run_batch(nufft_batch_s *b, void *const *c, void *const *f)
     }
     // grouped spreading / interpolation
     for (Group &g : b->groups) {
-        if (g.prec == 0) fill_args<float>(b->plans, g, c);
-        else fill_args<double>(b->plans, g, c);
-        cudaError_t e = cudaMemcpyAsync(g.d_args, g.h_args, g.args_bytes, cudaMemcpyHostToDevice, st);
+        void *host = g.graph_h_args, *dev = g.graph_d_args;
+        int slot = -1;
+        if (!for_graph) {
+            slot = g.ring_next;
+            g.ring_next = (g.ring_next + 1) % kRing;
+            cudaError_t e = cudaEventSynchronize(g.ev_ring[slot]);   // slot's last copy done
+            if (e != cudaSuccess) return cuda_rc(e);
+            host = g.h_ring[slot];
+            dev = g.d_args;
+        }
+        if (g.prec == 0) fill_args<float>(b->plans, g, c, host);
+        else fill_args<double>(b->plans, g, c, host);
+        cudaError_t e = cudaMemcpyAsync(dev, host, g.args_bytes, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_rc(e);
+        if (slot >= 0) {
+            e = cudaEventRecord(g.ev_ring[slot], st);
+            if (e != cudaSuccess) return cuda_rc(e);
+        }
         count_launch();
         batch_workoff_kernel<<<1, 32, 0, st>>>(g.d_nsub, g.d_ntransf, (int)g.members.size(),
                                                g.d_workoff);
         MultiLaunch ml;
-        ml.args = g.d_args;
+        ml.args = dev;
         ml.workoff = g.d_workoff;
         ml.nplans = (int)g.members.size();
         ml.w = g.w;
@@ -179,10 +207,6 @@ int run_batch(nufft_batch_s *b, void *const *c, void *const *f)
             rc = nufft_deconvolve(b->plans[k], f[k]);
             if (rc != NUFFT_OK) return rc;
         }
-    }
-    for (int k : b->singles) {
-        int rc = nufft_execute(b->plans[k], c[k], f[k]);
-        if (rc != NUFFT_OK) return rc;
     }
     return NUFFT_OK;
 }
@@ -213,10 +237,6 @@ int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_
         if (p.fft_ready && cufftSetStream(p.fft, p.stream) != CUFFT_SUCCESS) {
             free_batch(b);
             return NUFFT_ERR_CUFFT;
-        }
-        if (!groupable(p)) {
-            b->singles.push_back(k);
-            continue;
         }
         const int variant = sweep_variant(p);
         Group *g = nullptr;
@@ -252,7 +272,12 @@ int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_
             nt[i] = b->plans[g.members[i]]->p.ntransf;
         }
         cudaError_t e = cudaMalloc(&g.d_args, g.args_bytes);
-        if (e == cudaSuccess) e = cudaMallocHost(&g.h_args, g.args_bytes);
+        for (int i = 0; i < kRing && e == cudaSuccess; ++i) {
+            e = cudaMallocHost(&g.h_ring[i], g.args_bytes);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.ev_ring[i], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&g.graph_d_args, g.args_bytes);
+        if (e == cudaSuccess) e = cudaMallocHost(&g.graph_h_args, g.args_bytes);
         if (e == cudaSuccess) e = cudaMalloc((void **)&g.d_workoff, sizeof(int64_t) * (n + 1));
         if (e == cudaSuccess) e = cudaMalloc((void **)&g.d_nsub, sizeof(int32_t *) * n);
         if (e == cudaSuccess) e = cudaMalloc((void **)&g.d_ntransf, sizeof(int) * n);
@@ -272,7 +297,7 @@ int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_
 int nufft_batch_execute(nufft_batch b, void *const *c, void *const *f)
 {
     if (!b || !c || !f) return NUFFT_ERR_ARG;
-    return run_batch(b, c, f);
+    return run_batch(b, c, f, false);
 }
 
 int nufft_batch_capture(nufft_batch b, void *const *c, void *const *f)
@@ -287,9 +312,12 @@ int nufft_batch_capture(nufft_batch b, void *const *c, void *const *f)
         cudaGraphDestroy(b->graph);
         b->graph = nullptr;
     }
-    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    // a replay of the previous graph may still be reading its staging
+    cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_rc(e);
-    const int rc = run_batch(b, c, f);
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_rc(e);
+    const int rc = run_batch(b, c, f, true);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->stream, &g);
     if (rc != NUFFT_OK) {

@@ -128,6 +128,11 @@ __global__ void zero_kernel(uint4 *__restrict__ p, size_t n16)
         p[i] = z;
 }
 
+__global__ void set_int_kernel(int32_t *dst, int32_t v)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dst = v;
+}
+
 // p(k) for k = -floor(N/2) .. ceil(N/2)-1 along one axis, from the quadrature
 // nodes t_q and weights v_q = (pi/2) w_q exp(beta (cos t_q - 1)) cos t_q.
 template <typename T>
@@ -213,6 +218,13 @@ cudaError_t launch_zero(Plan &p, void *ptr, size_t bytes)
     if (blocks > cap) blocks = cap;
     count_launch();
     zero_kernel<<<(unsigned)blocks, 256, 0, p.stream>>>(reinterpret_cast<uint4 *>(ptr), n16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_int(Plan &p, int32_t *dst, int32_t value)
+{
+    count_launch();
+    set_int_kernel<<<1, 32, 0, p.stream>>>(dst, value);   // the value travels as a kernel argument
     return cudaGetLastError();
 }
 

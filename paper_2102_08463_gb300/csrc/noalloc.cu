@@ -10,10 +10,13 @@
 //
 // Limits: at most kMaxPoints points and kMaxBins bins per call.  The array is
 // about 8.1 MB and is resident on every device that loads this library, for the
-// life of the process.  Every call writes all the scratch it later reads, so
-// nothing in it has to start at zero; but all calls on one device share it, so
-// calls whose GPU work overlaps (different streams, or host threads) race and
-// must be serialised by the caller.
+// life of the process.  Under CUDA's lazy module loading the driver places it
+// (and loads the kernels) at the library's first use on a device, which may
+// allocate; a warm-up call per device at start-up (M = 0 suffices) moves that
+// cost out of the caller's allocation-free section.  Every call writes all the
+// scratch it later reads, so nothing in it has to start at zero; but all calls
+// on one device share it, so calls whose GPU work overlaps (different streams,
+// or host threads) race and must be serialised by the caller.
 #include <mutex>
 
 #include "nufft_internal.cuh"

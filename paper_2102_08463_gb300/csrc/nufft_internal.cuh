@@ -15,11 +15,21 @@ namespace nufft {
 
 constexpr int kMaxW = 16;
 
+// Raises a kernel's dynamic shared-memory limit to the device's maximum, once
+// per (kernel, current device); thread-safe.
+cudaError_t allow_max_smem(const void *func);
+
+// Fault injection (nufft_debug_fail): true if the armed failure of this kind
+// fires now; counts the calls of each kind.
+bool injected_failure(int kind);
+
 // Process-wide count of kernel launches made by this library.
 extern std::atomic<unsigned long long> g_launch_count;
 inline void count_launch(unsigned n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
 constexpr int kDefaultThreads = 256;
 constexpr int kPolyTerms = 17;     // polynomial degree <= 16
+// Points per work item of a GM plan in a batched launch.
+constexpr int kGmChunk = 2048;
 // Default 2D type 1 bins, sized for the row-sweep spreader: the padded width
 // m0 + w fills 8 lanes (w <= 3, single precision) or 16 lanes, so a warp
 // sweeps 4 or 2 points per step; taller bins in double precision and at
@@ -32,13 +42,18 @@ inline int default_bin_2d_type1(int axis, int prec, int w)
 }
 // Default bin sizes of a plan (1 on unused axes): 16 x 16 (2D) and 16 x 16 x 2
 // (3D), with the row-sweep sizes above for 2D type 1 and, for 3D single-precision
-// type 1 at w <= 4, 16 - w cells in x (16-lane sub-warps).
+// type 1 at w <= 8, (16 - w) x 32 x 2: the padded width fills 16-lane sub-warps
+// and the taller bin halves the row flushes per point (29 x 8 x 128 bins on a
+// 256^3 grid, within the shared-memory counting sort).
 inline void default_bins(int type, int dim, int prec, int w, int out[3])
 {
     for (int d = 0; d < 3; ++d) out[d] = d < dim ? (dim == 2 ? 16 : (d < 2 ? 16 : 2)) : 1;
     if (dim == 2 && type == 1)
         for (int d = 0; d < 2; ++d) out[d] = default_bin_2d_type1(d, prec, w);
-    if (dim == 3 && type == 1 && prec == 0 && w <= 4) out[0] = 16 - w;
+    if (dim == 3 && type == 1 && prec == 0 && w <= 8) {
+        out[0] = 16 - w;
+        out[1] = 32;
+    }
 }
 // Degree of the kernel polynomials: enough for 2e-8 (single) / 1e-14 (double)
 // on the interior window cells at every width.
@@ -52,7 +67,8 @@ template <> struct cplx<double> { using type = double2; };
 // Packed per-point record: kernel offsets delta_i = u_i - l0_i
 // (u_i the fine-grid coordinate, l0_i the first window cell) and the window
 // start relative to the padded bin, three 10-bit fields in one 32-bit word
-// stored in the last slot.
+// stored in the last slot.  In 2D the z slot holds the point's original index
+// (as the bits of a 32-bit word).
 template <typename T> struct rec4;
 template <> struct rec4<float> { using type = float4; };
 template <> struct rec4<double> { using type = double4_32a; };
@@ -199,13 +215,15 @@ struct Plan {
     int32_t *vals = nullptr;       // [Mcap]
     int32_t *vals_alt = nullptr;   // [Mcap]
     int32_t *perm = nullptr;       // [Mcap] t: sorted position -> original index
-    void *recs = nullptr;          // [Mcap] rec4<T> per point, original order
+    void *recs = nullptr;          // [Mcap] rec4<T> per point, execution order (see setpts.cu)
+    void *recs_in = nullptr;       // [Mcap] rec4<T> per point, original order (setpts scratch)
+    int32_t *order = nullptr;      // [Mcap] 3D: execution position -> original index
     void *xyz_copy[3] = {nullptr, nullptr, nullptr};  // coordinate copies for GM
     int32_t *bincount = nullptr;   // [nbins]
     int32_t *binstart = nullptr;   // [nbins]
     int4 *subprob = nullptr;       // [maxsub] (bin, start, count, 0)
     int64_t maxsub = 0;
-    int32_t *nsub = nullptr;       // [1] device scalar
+    int32_t *nsub = nullptr;       // [1] device scalar: subproblems (GM: kGmChunk chunks)
     int32_t *mat = nullptr;        // sort histogram matrix (bins or digits) x CTAs
     int64_t mat_cap = 0;
     int32_t *scan_part = nullptr;  // block sums of the multi-block scan
@@ -221,6 +239,16 @@ struct Plan {
     bool poly_ok = false;
     bool use_picker = false;       // consult the installed tile picker at setpts
     bool unordered_bins = false;   // counting-sort scatter in shared-atomic order
+    bool debug_checks = false;     // device-side checks at setpts (status word)
+    int32_t *dstatus = nullptr;    // [1] device status of the checks (0 = passed)
+
+    // host-buffer execute (nufft_execute_host): device staging, grown on demand
+    void *hx_pts[3] = {nullptr, nullptr, nullptr};   // coordinates [hx_cap]
+    void *hx_c = nullptr;          // ntransf * M complex
+    void *hx_f = nullptr;          // ntransf * Ntot complex
+    int64_t hx_cap = 0;            // points the staging holds
+    cudaStream_t hx_copy = nullptr;   // stream of the input copy
+    cudaEvent_t hx_ev[2] = {nullptr, nullptr};   // entry, input copied
 };
 
 // Tile settings of a plan (method, bin sizes, subproblem cap, threads per CTA).
@@ -258,6 +286,8 @@ int kernel_width(double eps, double sigma);
 // cudaError_t from the last launch.
 cudaError_t launch_setpts(Plan &p, const void *x, const void *y, const void *z);
 cudaError_t launch_scan(Plan &p, const int32_t *in, int32_t *out, int64_t L, int32_t *total);
+// debug_checks: coordinates finite and in [-3 pi, 3 pi]; t a permutation of 0..M-1.
+cudaError_t launch_checks(Plan &p, const void *x, const void *y, const void *z);
 
 // Scratch of the bin-sort when the caller supplies it (allocation-free entry point).
 struct BinsortScratch {
@@ -313,6 +343,8 @@ cudaError_t interp_multi_f64_3d(const MultiLaunch &ml);
 cudaError_t launch_deconvolve(Plan &p, void *f);
 cudaError_t launch_precorrect(Plan &p, const void *f);
 cudaError_t launch_zero(Plan &p, void *ptr, size_t bytes);
+// Stores value in the device int *dst on the plan's stream.
+cudaError_t launch_set_int(Plan &p, int32_t *dst, int32_t value);
 cudaError_t launch_correction(Plan &p, const double *gl_t, const double *gl_w, int nq);
 
 }  // namespace nufft

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -13,6 +14,57 @@
 using namespace nufft;
 
 std::atomic<unsigned long long> nufft::g_launch_count{0};
+
+namespace {
+std::atomic<int> g_fail_after[3] = {{-1}, {-1}, {-1}};   // armed countdown per kind
+std::atomic<int> g_fail_calls[3] = {{0}, {0}, {0}};     // calls since the last arming
+}  // namespace
+
+bool nufft::injected_failure(int kind)
+{
+    if (kind < 1 || kind > 2) return false;
+    g_fail_calls[kind].fetch_add(1);
+    int left = g_fail_after[kind].load();
+    while (left >= 0) {
+        if (g_fail_after[kind].compare_exchange_weak(left, left - 1)) return left == 0;
+    }
+    return false;
+}
+
+// Each kernel's dynamic shared-memory limit is raised once per device, to the
+// largest the device allows next to the kernel's static shared memory, so that
+// no launch depends on a per-call setting another host thread could change.
+// The (kernel, device) pairs already done sit in a fixed table (no heap use);
+// past its end the attribute is simply set again, to the same value.
+cudaError_t nufft::allow_max_smem(const void *func)
+{
+    constexpr int kCap = 1024;
+    static std::mutex mu;
+    static const void *done_f[kCap];
+    static int done_d[kCap];
+    static int ndone = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < ndone; ++i)
+        if (done_f[i] == func && done_d[i] == dev) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn > 0 ? dyn : 0);
+    if (e != cudaSuccess) return e;
+    if (ndone < kCap) {
+        done_f[ndone] = func;
+        done_d[ndone] = dev;
+        ++ndone;
+    }
+    return cudaSuccess;
+}
 
 int nufft::next235(int64_t n)
 {
@@ -84,6 +136,7 @@ template <typename Ptr>
 int dev_alloc(Ptr **ptr, size_t bytes)
 {
     *ptr = nullptr;
+    if (injected_failure(NUFFT_FAIL_ALLOC)) return NUFFT_ERR_ALLOC;
     if (bytes == 0) bytes = 16;
     void *v = nullptr;
     cudaError_t e = cudaMalloc(&v, bytes);
@@ -107,6 +160,8 @@ void free_points(Plan &p)
     dev_free(p.vals);
     dev_free(p.vals_alt);
     dev_free(p.recs);
+    dev_free(p.recs_in);
+    dev_free(p.order);
     dev_free(p.subprob);
     for (int d = 0; d < 3; ++d) {
         dev_free(p.xyz_copy[d]);
@@ -114,20 +169,43 @@ void free_points(Plan &p)
     }
     p.keys = p.keys_alt = p.vals = p.vals_alt = p.perm = nullptr;
     p.recs = nullptr;
+    p.recs_in = nullptr;
+    p.order = nullptr;
     p.subprob = nullptr;
     p.Mcap = 0;
     p.maxsub = 0;
 }
 
+void free_host_staging(Plan &p)
+{
+    for (int d = 0; d < 3; ++d) {
+        dev_free(p.hx_pts[d]);
+        p.hx_pts[d] = nullptr;
+    }
+    dev_free(p.hx_c);
+    p.hx_c = nullptr;
+    p.hx_cap = 0;
+}
+
 void free_plan(Plan &p)
 {
     free_points(p);
+    free_host_staging(p);
+    dev_free(p.hx_f);
+    p.hx_f = nullptr;
+    for (int i = 0; i < 2; ++i)
+        if (p.hx_ev[i]) cudaEventDestroy(p.hx_ev[i]);
+    if (p.hx_copy) cudaStreamDestroy(p.hx_copy);
+    p.hx_copy = nullptr;
+    p.hx_ev[0] = p.hx_ev[1] = nullptr;
     dev_free(p.fine);
     for (int d = 0; d < 3; ++d) dev_free(p.corr[d]);
     dev_free(p.bincount);
     dev_free(p.binstart);
     dev_free(p.scan_tmp);
     dev_free(p.nsub);
+    dev_free(p.dstatus);
+    p.dstatus = nullptr;
     dev_free(p.mat);
     dev_free(p.scan_part);
     p.mat = p.scan_part = nullptr;
@@ -290,7 +368,7 @@ const char *nufft_strerror(int code)
     case NUFFT_ERR_CUDA: return "CUDA error";
     case NUFFT_ERR_CUFFT: return "cuFFT error";
     case NUFFT_ERR_NOPTS: return "execute called before setpts";
-    case NUFFT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case NUFFT_ERR_CHECK: return "a device-side check failed (debug_checks)";
     case NUFFT_ERR_METHOD: return "method not available for this plan";
     default: return "unknown error";
     }
@@ -388,6 +466,7 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
                    o.bin[2] == 0 && o.msub == 0 && o.threads == 0;
     p.use_picker = p.auto_tiles && o.use_picker != 0;
     p.unordered_bins = o.unordered_bins != 0;
+    p.debug_checks = o.debug_checks != 0;
     if (p.method == NUFFT_METHOD_SM) {
         size_t cells = 1;
         for (int d = 0; d < dim; ++d) cells *= (size_t)padded(p.m[d], w);
@@ -403,6 +482,11 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     if (rc == NUFFT_OK) rc = dev_alloc(&p.binstart, sizeof(int32_t) * p.nbins);
     if (rc == NUFFT_OK) rc = dev_alloc(&p.scan_tmp, sizeof(int32_t) * p.nbins);
     if (rc == NUFFT_OK) rc = dev_alloc(&p.nsub, sizeof(int32_t) * 4);
+    if (rc == NUFFT_OK && p.debug_checks) {
+        rc = dev_alloc(&p.dstatus, sizeof(int32_t));
+        if (rc == NUFFT_OK && cudaMemsetAsync(p.dstatus, 0, sizeof(int32_t), p.stream) != cudaSuccess)
+            rc = NUFFT_ERR_CUDA;
+    }
     if (rc != NUFFT_OK) {
         free_plan(p);
         delete h;
@@ -453,8 +537,11 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     {
         int dims[3];
         for (int d = 0; d < dim; ++d) dims[d] = (int)p.nf[dim - 1 - d];   // slowest first
-        cufftResult r = cufftPlanMany(&p.fft, dim, dims, nullptr, 1, (int)nftot, nullptr, 1,
-                                      (int)nftot, p.prec == 0 ? CUFFT_C2C : CUFFT_Z2Z, ntransf);
+        cufftResult r = injected_failure(NUFFT_FAIL_CUFFT)
+                            ? CUFFT_INTERNAL_ERROR
+                            : cufftPlanMany(&p.fft, dim, dims, nullptr, 1, (int)nftot, nullptr, 1,
+                                            (int)nftot, p.prec == 0 ? CUFFT_C2C : CUFFT_Z2Z,
+                                            ntransf);
         if (r == CUFFT_SUCCESS) {
             p.fft_ready = true;
             r = cufftSetStream(p.fft, p.stream);
@@ -501,6 +588,8 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
         if (rc == NUFFT_OK) rc = dev_alloc(&p.vals, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.vals_alt, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.recs, rsz * cap);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.recs_in, rsz * cap);
+        if (rc == NUFFT_OK && p.dim == 3) rc = dev_alloc(&p.order, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.subprob, sizeof(int4) * maxsub);
         if (rc != NUFFT_OK) {
             free_points(p);
@@ -523,6 +612,9 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
                                             cudaMemcpyDeviceToDevice, p.stream);
             if (e != cudaSuccess) return cuda_err(e);
         }
+        // work count of the plan in a batched launch: chunks of kGmChunk points
+        cudaError_t e = launch_set_int(p, p.nsub, (int32_t)((M + kGmChunk - 1) / kGmChunk));
+        if (e != cudaSuccess) return cuda_err(e);
         p.M = M;
         p.have_pts = true;
         return NUFFT_OK;
@@ -556,6 +648,7 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
         }
     }
     cudaError_t e = launch_setpts(p, x, y, z);
+    if (e == cudaSuccess && p.debug_checks) e = launch_checks(p, x, y, z);
     if (e != cudaSuccess) return cuda_err(e);
     p.have_pts = true;
     return NUFFT_OK;
@@ -645,6 +738,70 @@ int nufft_execute(nufft_plan h, void *c, void *f)
     return nufft_interp(h, c);
 }
 
+int nufft_execute_host(nufft_plan h, int64_t M, const void *x, const void *y, const void *z,
+                       void *c, void *f)
+{
+    if (!h || !f) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (M < 0 || M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_ARG;
+    if (M > 0 && (!x || !y || (p.dim == 3 && !z) || !c)) return NUFFT_ERR_ARG;
+    const size_t rs = real_size(p), cs = 2 * rs;
+    int rc = NUFFT_OK;
+    // staging and the copy stream, made once and grown with M
+    if (!p.hx_copy) {
+        cudaError_t e = cudaStreamCreateWithFlags(&p.hx_copy, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&p.hx_ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    if (!p.hx_f) {
+        rc = dev_alloc(&p.hx_f, (size_t)p.Ntot * p.ntransf * cs);
+        if (rc != NUFFT_OK) return rc;
+    }
+    if (M > p.hx_cap) {
+        free_host_staging(p);
+        for (int d = 0; d < p.dim && rc == NUFFT_OK; ++d) rc = dev_alloc(&p.hx_pts[d], rs * M);
+        if (rc == NUFFT_OK) rc = dev_alloc(&p.hx_c, cs * (size_t)M * p.ntransf);
+        if (rc != NUFFT_OK) {
+            free_host_staging(p);
+            return rc;
+        }
+        p.hx_cap = M;
+    }
+    cudaStream_t st = p.stream;
+    // the staging may still be in use by the previous call's kernels
+    cudaError_t e = cudaEventRecord(p.hx_ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p.hx_copy, p.hx_ev[0], 0);
+    // points first, on the plan stream, so the sort starts as soon as they arrive
+    const void *src[3] = {x, y, z};
+    for (int d = 0; d < p.dim && M > 0 && e == cudaSuccess; ++d)
+        e = cudaMemcpyAsync(p.hx_pts[d], src[d], rs * M, cudaMemcpyHostToDevice, st);
+    // the input of the transform on the copy stream, overlapping the sort
+    if (e == cudaSuccess) {
+        if (p.type == 1) {
+            if (M > 0)
+                e = cudaMemcpyAsync(p.hx_c, c, cs * (size_t)M * p.ntransf, cudaMemcpyHostToDevice,
+                                    p.hx_copy);
+        } else {
+            e = cudaMemcpyAsync(p.hx_f, f, cs * (size_t)p.Ntot * p.ntransf, cudaMemcpyHostToDevice,
+                                p.hx_copy);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(p.hx_ev[1], p.hx_copy);
+    if (e != cudaSuccess) return cuda_err(e);
+    rc = nufft_setpts(h, M, p.hx_pts[0], p.hx_pts[1], p.dim == 3 ? p.hx_pts[2] : nullptr);
+    if (rc != NUFFT_OK) return rc;
+    e = cudaStreamWaitEvent(st, p.hx_ev[1], 0);
+    if (e != cudaSuccess) return cuda_err(e);
+    rc = nufft_execute(h, p.hx_c, p.hx_f);
+    if (rc != NUFFT_OK) return rc;
+    if (p.type == 1)
+        e = cudaMemcpyAsync(f, p.hx_f, cs * (size_t)p.Ntot * p.ntransf, cudaMemcpyDeviceToHost, st);
+    else if (M > 0)
+        e = cudaMemcpyAsync(c, p.hx_c, cs * (size_t)M * p.ntransf, cudaMemcpyDeviceToHost, st);
+    return cuda_err(e);
+}
+
 uint64_t nufft_get_launch_count(void)
 {
     return (uint64_t)g_launch_count.load(std::memory_order_relaxed);
@@ -693,6 +850,27 @@ int nufft_get_tiles(nufft_plan h, nufft_opts *out)
     out->msub = p.msub;
     out->threads = p.threads;
     return NUFFT_OK;
+}
+
+int nufft_get_status(nufft_plan h)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (!p.debug_checks || !p.dstatus) return NUFFT_OK;
+    int32_t v = 0;
+    cudaError_t e = cudaStreamSynchronize(p.stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p.dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v != 0) e = cudaMemset(p.dstatus, 0, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_err(e);
+    return v != 0 ? NUFFT_ERR_CHECK : NUFFT_OK;
+}
+
+int nufft_debug_fail(int kind, int after)
+{
+    if (kind != NUFFT_FAIL_ALLOC && kind != NUFFT_FAIL_CUFFT) return NUFFT_ERR_ARG;
+    const int calls = g_fail_calls[kind].exchange(0);
+    g_fail_after[kind].store(after < 0 ? -1 : after);
+    return calls;
 }
 
 int nufft_get_sort(nufft_plan h, int32_t *t, int32_t *bincounts, int32_t *nsub)

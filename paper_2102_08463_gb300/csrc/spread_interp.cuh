@@ -28,8 +28,8 @@ constexpr unsigned kFullMask = 0xffffffffu;
 
 template <typename T>
 struct alignas(16) KArgs {
-    const typename rec4<T>::type *recs;
-    const int32_t *perm;
+    const typename rec4<T>::type *recs;          // packed records, execution order
+    const int32_t *order;                        // 3D: execution position -> point index
     const int4 *subprob;
     const int32_t *nsub;
     const T *xyz0, *xyz1, *xyz2;                 // coordinates (GM kernels)
@@ -54,6 +54,41 @@ template <> __device__ __forceinline__ uint32_t unpack_word<float>(float v) { re
 template <> __device__ __forceinline__ uint32_t unpack_word<double>(double v)
 {
     return (uint32_t)__double_as_longlong(v);
+}
+
+// Original index of the point at execution position pos with record r: in 2D
+// the record's z slot, in 3D the order array.
+template <typename T, int DIM>
+__device__ __forceinline__ int point_of(const KArgs<T> &a, const typename rec4<T>::type &r,
+                                        int64_t pos)
+{
+    return DIM == 2 ? (int)unpack_word<T>(r.z) : a.order[pos];
+}
+
+// Packed single-precision pairs: two floats in one 64-bit register pair, for
+// the f32x2 arithmetic of sm_100-class GPUs (one instruction for both lanes).
+__device__ __forceinline__ uint64_t pack2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+// acc += a * b, lane by lane
+__device__ __forceinline__ void fma2(uint64_t &acc, uint64_t a, uint64_t b)
+{
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
 }
 
 __device__ __forceinline__ int wrap_any(int v, int n)
@@ -137,9 +172,9 @@ __device__ __forceinline__ void spread_sm_item(const KArgs<T> &a, int sp, int tr
             C cv;
             cv.x = cv.y = (T)0;
             if (base + lane < sub.z) {
-                const int j = a.perm[sub.y + base + lane];
-                r = a.recs[j];
-                cv = cin[j];
+                const int64_t pos = sub.y + base + lane;
+                r = a.recs[pos];
+                cv = cin[point_of<T, DIM>(a, r, pos)];
             }
             const int np = min(32, sub.z - base);
             for (int i0 = 0; i0 < np; i0 += G) {
@@ -241,41 +276,50 @@ spread_sm_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restr
 // padded bin (p0 = m0 + W <= L) and holds, in registers, the W rows that a
 // window starting at the current row can reach.
 //
-//  1. The subproblem's points are ordered by the first row of their window
-//     (stable counting sort in shared memory: warp-aggregated integer atomics).
-//  2. 32 points at a time, lane i evaluates point i's 2W kernel values and
-//     stores w_y and c w_x in a staging slot.
+//  1. setpts left the subproblem's records ordered by the first row of their
+//     window (then column; see setpts.cu), so the warp reads them as one
+//     contiguous run, 32 at a time, with the strengths c gathered by index.
+//  2. Lane i evaluates point i's 2W kernel values and stores w_y and c w_x in a
+//     staging slot.
 //  3. The warp walks the staged points one start row at a time.  Before row r
 //     is entered, every row above r is complete: the sub-warps' copies of it are
 //     summed by shuffles, added to the fine grid (periodic wrap), and the
 //     register window shifts down one row.  The points starting at row r are
 //     dealt to the sub-warps in turn; every lane adds (c w_x[q - s_x]) w_y[k] to
 //     its W rows -- a plain register update, since within a sub-warp no two
-//     lanes own the same cell.
+//     lanes own the same cell.  In single precision each row is one packed
+//     (re, im) register pair updated by one f32x2 FMA.  A start row lower than
+//     the current one (a new ordering piece of a long subproblem) flushes the
+//     whole window first.
 //  4. The rows still held at the end are added to the fine grid.
 //
-// Shared memory per warp (sweep_bytes): order[msub] and keys[msub] (uint16), the
-// row cursors (m1 + 2 ints) and 32 staging slots.
+// Shared memory per warp (sweep_bytes): 32 staging slots.
 // ---------------------------------------------------------------------------
-// Staging slots are built from 16-byte quads (4 floats or 2 doubles): each
-// weight row takes QW = ceil(W / VEC) quads, the key word one more, and the
-// quad count is made odd so that the 8 lanes of a quarter-warp storing their
-// slots with 128-bit stores hit 8 different bank quads.
+// Staging slots are built from 16-byte quads (4 floats or 2 doubles), with an
+// odd quad count so that the 8 lanes of a quarter-warp storing their slots with
+// 128-bit stores hit 8 different bank quads.
 template <typename T> __host__ __device__ constexpr int quad_vec() { return 16 / (int)sizeof(T); }
 template <typename T, int W> __host__ __device__ constexpr int quad_row()
 {
     return (W + quad_vec<T>() - 1) / quad_vec<T>();
 }
-// 2D slot: w_y row, then c w_x scattered into an L-wide complex row (zeros
-// outside the window), so lane q reads entry q at a fixed address.
+// 2D slot: the W row weights (single precision: W duplicated pairs (w_y, w_y),
+// (W + 1) / 2 quads; double: W values), then c w_x scattered into an L-wide
+// complex row (zeros outside the window), so lane q reads entry q at a fixed
+// address.
+template <typename T, int W> __host__ __device__ constexpr int sweep2_wy_quads()
+{
+    return sizeof(T) == 4 ? (W + 1) / 2 : quad_row<T, W>();
+}
 template <typename T, int W, int L> __host__ __device__ constexpr int sweep2_slot()
 {
-    return ((quad_row<T, W>() + 2 * L / quad_vec<T>()) | 1) * quad_vec<T>();
+    return ((sweep2_wy_quads<T, W>() + 2 * L * (int)sizeof(T) / 16) | 1) * quad_vec<T>();
 }
-// 3D slot: w_y, w_z, the L-wide c w_x row, key word.
+// 3D slot (single precision): w_y and w_z as duplicated pairs ((W + 1) / 2
+// quads each), then the L-wide c w_x row.
 template <typename T, int W, int L> __host__ __device__ constexpr int sweep3_slot()
 {
-    return ((2 * quad_row<T, W>() + 2 * L / quad_vec<T>() + 1) | 1) * quad_vec<T>();
+    return ((2 * ((W + 1) / 2) + 2 * L / quad_vec<T>()) | 1) * quad_vec<T>();
 }
 
 __device__ __forceinline__ void store_zero_quad(float *dst)
@@ -312,26 +356,21 @@ __device__ __forceinline__ void store_row(double *dst, const double (&v)[W])
         *reinterpret_cast<double2 *>(dst + k) = t;
     }
 }
-
-// The row sweeps take a subproblem in pieces of at most kSweepCap points (each
-// piece sorted, swept and flushed on its own), so their shared memory does not
-// grow with M_sub -- the rest of the SM's 256 KB stays L1 cache for the gathers.
-constexpr int kSweepCap = 512;
-
-// Byte offsets inside a warp's shared memory: order[msub] and keys[msub]
-// (uint16) at 0, the row cursors at sweep_cur, the staging slots at sweep_head
-// (16-byte aligned).
-__host__ __device__ inline size_t sweep_cur(int msub) { return (size_t)4 * msub; }
-// nkeys = number of distinct sort keys (2D: m1 + 1 start rows; 3D: (m1 + 1)(m2 + 1)).
-__host__ __device__ inline size_t sweep_head(int msub, int nkeys)
+// Stores the W values as duplicated pairs (v, v), two pairs per quad.
+template <int W>
+__device__ __forceinline__ void store_dup_row(float *dst, const float (&v)[W])
 {
-    return (sweep_cur(msub) + (size_t)4 * (nkeys + 1) + 15) & ~(size_t)15;
+#pragma unroll
+    for (int k = 0; k < W; k += 2) {
+        const float b = k + 1 < W ? v[k + 1 < W ? k + 1 : k] : 0.f;
+        *reinterpret_cast<float4 *>(dst + 2 * k) = make_float4(v[k], v[k], b, b);
+    }
 }
 
 template <typename T, int W, int L>
-__host__ __device__ inline size_t sweep_bytes(int msub, int m1)
+__host__ __device__ inline size_t sweep_bytes()
 {
-    return sweep_head(msub, m1 + 1) + sizeof(T) * (size_t)32 * sweep2_slot<T, W, L>();
+    return sizeof(T) * (size_t)32 * sweep2_slot<T, W, L>();
 }
 
 // Single-precision ES kernel for the staging step, written without the
@@ -416,95 +455,17 @@ __device__ __forceinline__ void load_row(const double *s, double (&v)[W])
     }
 }
 
-// Stable counting sort of a subproblem's n points by the first row of their
-// window: the row fields of the points' packed words are gathered through t
-// (eight loads in flight per lane) into keys[], then counted and ranked with
-// warp-aggregated integer atomics.  order[] receives the point indices grouped
-// by row, increasing index within a row.  One warp; cur[] holds nrow + 1
-// cursors.
-template <typename T, int ZMUL>
-__device__ __forceinline__ void sweep_row_sort(const typename rec4<T>::type *recs,
-                                               const int32_t *perm, int n, int nrow,
-                                               uint16_t *order, uint16_t *keys, int *cur)
-{
-    constexpr int U = 8;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int i = lane; i <= nrow; i += 32) cur[i] = 0;
-    for (int base = 0; base < n; base += 32 * U) {
-        uint32_t w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = base + u * 32 + lane;
-            w[u] = k < n ? unpack_word<T>(recs[perm[k]].w) : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = base + u * 32 + lane;
-            // 2D: key = window start row; 3D: start row * (m2 + 1) + start plane
-            if (k < n)
-                keys[k] = (uint16_t)(ZMUL == 0 ? ((w[u] >> 10) & 1023u)
-                                               : ((w[u] >> 10) & 1023u) * ZMUL + (w[u] >> 20));
-        }
-    }
-    __syncwarp();
-    for (int base = 0; base < n; base += 32) {
-        const int k = base + lane;
-        const int key = k < n ? (int)keys[k] : 0x7fffffff;
-        const unsigned peers = __match_any_sync(kFullMask, key);
-        if (k < n && (peers & lt) == 0) atomicAdd(&cur[key + 1], __popc(peers));
-    }
-    __syncwarp();
-    int running = 0;
-    for (int i0 = 1; i0 <= nrow; i0 += 32) {
-        const int i = i0 + lane;
-        int v = i <= nrow ? cur[i] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFullMask, v, o);
-            if (lane >= o) v += t;
-        }
-        if (i <= nrow) cur[i] = running + v;
-        running += __shfl_sync(kFullMask, v, 31);
-    }
-    __syncwarp();
-    for (int base = 0; base < n; base += 32) {
-        const int k = base + lane;
-        const int key = k < n ? (int)keys[k] : 0x7fffffff;
-        const unsigned peers = __match_any_sync(kFullMask, key);
-        const int leader = __ffs(peers) - 1;
-        int pos = 0;
-        if (k < n && lane == leader) pos = atomicAdd(&cur[key], __popc(peers));
-        pos = __shfl_sync(kFullMask, pos, leader);
-        if (k < n) order[pos + __popc(peers & lt)] = (uint16_t)k;
-    }
-    __syncwarp();
-}
-
 template <typename T, int W, int L>
-__device__ __forceinline__ void spread_sweep2_piece(const KArgs<T> &a, int4 sub, int tr,
-                                                    unsigned char *sm)
+__device__ __forceinline__ void spread_sweep2_sub(const KArgs<T> &a, int4 sub, int tr, T *stg)
 {
-    constexpr int msub = kSweepCap;
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
+    constexpr bool F32 = sizeof(T) == 4;
     constexpr int S = 32 / L;
     constexpr int SLOT = sweep2_slot<T, W, L>();
-    constexpr int OWY = 0, OCX = quad_row<T, W>() * quad_vec<T>();
+    constexpr int OCX = sweep2_wy_quads<T, W>() * quad_vec<T>();
     const int lane = threadIdx.x & 31, h = lane / L, q = lane % L;
     const int n = sub.z;
-    uint16_t *order = reinterpret_cast<uint16_t *>(sm);
-    uint16_t *keys = order + msub;
-    int *cur = reinterpret_cast<int *>(sm + sweep_cur(msub));
-    T *stg = reinterpret_cast<T *>(sm + sweep_head(msub, a.m1 + 1));
-    const int nrow = a.m1 + 1;                            // window start rows 0 .. m1
-    const int32_t *perm = a.perm + sub.y;
-
-    // 1. stable counting sort of the points by window start row
-    sweep_row_sort<T, 0>(a.recs, perm, n, nrow, order, keys, cur);
-
-    // 2.-4. stage and sweep; the next batch's gathers are issued before the
-    // current batch is swept
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
     const int P = pad_lo(W);
@@ -513,10 +474,15 @@ __device__ __forceinline__ void spread_sweep2_piece(const KArgs<T> &a, int4 sub,
     const bool writer = h == 0 && q < a.p0;
     const int gx = wrap_any(o0 - P + (q < a.p0 ? q : 0), a.n0);
     const int row0 = o1 - P;
-    T accr[W], acci[W];
+    // window row k: accp[k] = (re, im) packed (single), accr[k] / acci[k] (double)
+    uint64_t accp[F32 ? W : 1];
+    T accr[F32 ? 1 : W], acci[F32 ? 1 : W];
 #pragma unroll
-    for (int r = 0; r < W; ++r) accr[r] = acci[r] = (T)0;
-    int row = 0;                                          // padded row held in acc[0]
+    for (int k = 0; k < W; ++k) {
+        if constexpr (F32) accp[k] = 0ull;
+        else accr[k] = acci[k] = (T)0;
+    }
+    int row = 0;                                          // padded row held in row slot 0
 
     auto flush_row = [&](int r_rel, T vr, T vi) {
 #pragma unroll
@@ -527,14 +493,21 @@ __device__ __forceinline__ void spread_sweep2_piece(const KArgs<T> &a, int4 sub,
         if (writer && (vr != (T)0 || vi != (T)0))
             atomic_add_cplx(&grid[(int64_t)wrap_any(row0 + r_rel, a.n1) * a.n0 + gx], vr, vi);
     };
+    auto flush_slot = [&](int k, int r_rel) {
+        if constexpr (F32) {
+            const float2 v = unpack2(accp[k < W ? k : 0]);
+            flush_row(r_rel, v.x, v.y);
+        } else {
+            flush_row(r_rel, accr[k < W ? k : 0], acci[k < W ? k : 0]);
+        }
+    };
 
     R rc;
     C cv;
     auto fetch = [&](int base) {
         if (base + lane < n) {
-            const int j = perm[order[base + lane]];
-            rc = a.recs[j];
-            cv = cin[j];
+            rc = a.recs[sub.y + base + lane];
+            cv = cin[unpack_word<T>(rc.z)];
         }
     };
     fetch(0);
@@ -558,34 +531,62 @@ __device__ __forceinline__ void spread_sweep2_piece(const KArgs<T> &a, int4 sub,
                 v.y = cv.y * vx[i];
                 *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) = v;
             }
-            store_row<W>(s + OWY, vy);
+            if constexpr (F32) store_dup_row<W>(s, vy);
+            else store_row<W>(s, vy);
         }
+        if (base == 0) row = __shfl_sync(kFullMask, myrow, 0);
         fetch(base + 32);
         __syncwarp();
         int i0 = 0;
         while (i0 < cnt) {
             const int r = __shfl_sync(kFullMask, myrow, i0);
-            while (row < r) {
-                flush_row(row, accr[0], acci[0]);
+            if (r != row) {
+                if (r > row && r < row + W) {
+                    do {                                  // rows above r are complete
+                        flush_slot(0, row);
 #pragma unroll
-                for (int k = 0; k + 1 < W; ++k) {
-                    accr[k] = accr[k + 1];
-                    acci[k] = acci[k + 1];
+                        for (int k = 0; k + 1 < W; ++k) {
+                            if constexpr (F32) accp[k] = accp[k + 1];
+                            else {
+                                accr[k] = accr[k + 1];
+                                acci[k] = acci[k + 1];
+                            }
+                        }
+                        if constexpr (F32) accp[W - 1] = 0ull;
+                        else accr[W - 1] = acci[W - 1] = (T)0;
+                        ++row;
+                    } while (row < r);
+                } else {                                  // jump: the whole window is complete
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        flush_slot(k, row + k);
+                        if constexpr (F32) accp[k] = 0ull;
+                        else accr[k] = acci[k] = (T)0;
+                    }
+                    row = r;
                 }
-                accr[W - 1] = acci[W - 1] = (T)0;
-                ++row;
             }
-            const unsigned later = __ballot_sync(kFullMask, myrow > r) & ~((2u << i0) - 1u);
+            const unsigned later = __ballot_sync(kFullMask, myrow != r) & ~((2u << i0) - 1u);
             const int i1 = later ? __ffs(later) - 1 : cnt;
             for (int i = i0 + h; i < i1; i += S) {
                 const T *s = stg + i * SLOT;
-                const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * q);
-                T wy[W];
-                load_row<W>(s + OWY, wy);
+                if constexpr (F32) {
+                    const uint64_t cx = *reinterpret_cast<const uint64_t *>(s + OCX + 2 * q);
 #pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    accr[k] += cx.x * wy[k];
-                    acci[k] += cx.y * wy[k];
+                    for (int k = 0; k < W; k += 2) {
+                        const ulonglong2 wp = *reinterpret_cast<const ulonglong2 *>(s + 2 * k);
+                        fma2(accp[k], cx, wp.x);
+                        if (k + 1 < W) fma2(accp[k + 1 < W ? k + 1 : k], cx, wp.y);
+                    }
+                } else {
+                    const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * q);
+                    T wy[W];
+                    load_row<W>(s, wy);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        accr[k] += cx.x * wy[k];
+                        acci[k] += cx.y * wy[k];
+                    }
                 }
             }
             i0 = i1;
@@ -593,62 +594,50 @@ __device__ __forceinline__ void spread_sweep2_piece(const KArgs<T> &a, int4 sub,
         __syncwarp();
     }
 #pragma unroll
-    for (int r = 0; r < W; ++r) flush_row(row + r, accr[r], acci[r]);
+    for (int k = 0; k < W; ++k) flush_slot(k, row + k);
 }
 
 // ---------------------------------------------------------------------------
 // Row-sweep SM spreading, 3D (single precision, W <= 8, bins m2 = M2 in {1, 2}).
 // As the 2D sweep: S = 32 / L sub-warps, lane q owns x column q of the padded
 // bin (p0 <= L) and holds the W y rows in reach times all M2 + W z planes in
-// registers.  The points are ordered by (window start row, start plane); the
-// points of one (row, plane) group are dealt to the sub-warps, so the first
+// registers.  The records come ordered by (window start row, start plane) from
+// setpts; the points of one (row, plane) group are dealt to the sub-warps, so the first
 // plane s_z is the same for the whole warp and selects one of M2 + 1 unrolled
 // updates  acc[j][s_z + k] += (c w_x[q - s_x] w_y[j]) w_z[k],  j, k < W.
 // A finished row is summed over the sub-warps and added to the fine grid plane
 // by plane.
 // ---------------------------------------------------------------------------
-template <typename T, int W, int M2, int L>
-__host__ __device__ inline size_t sweep3_bytes(int msub, int m1)
+template <typename T, int W, int L>
+__host__ __device__ inline size_t sweep3_bytes()
 {
-    return sweep_head(msub, (m1 + 1) * (M2 + 1)) + sizeof(T) * (size_t)32 * sweep3_slot<T, W, L>();
+    return sizeof(T) * (size_t)32 * sweep3_slot<T, W, L>();
 }
 
-template <typename T, int W, int PZ, int O>
-__device__ __forceinline__ void sweep3_add(T (&ar)[W][PZ], T (&ai)[W][PZ], const T (&t)[W],
-                                           const T (&u)[W], const T (&wz)[W])
+// acc[j][O + k] += tu[j] * wzz[k], packed (re, im) pairs
+template <int W, int PZ, int O>
+__device__ __forceinline__ void sweep3_add(uint64_t (&acc)[W][PZ], const uint64_t (&tu)[W],
+                                           const uint64_t (&wzz)[W])
 {
 #pragma unroll
     for (int j = 0; j < W; ++j) {
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            ar[j][O + k] += t[j] * wz[k];
-            ai[j][O + k] += u[j] * wz[k];
-        }
+        for (int k = 0; k < W; ++k) fma2(acc[j][O + k], tu[j], wzz[k]);
     }
 }
 
 template <typename T, int W, int M2, int L>
-__device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub, int tr,
-                                                    unsigned char *sm)
+__device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, int tr, T *stg)
 {
-    constexpr int msub = kSweepCap;
+    static_assert(sizeof(T) == 4, "the 3D row sweep is single precision");
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
     constexpr int S = 32 / L;
     constexpr int PZ = M2 + W;
     constexpr int SLOT = sweep3_slot<T, W, L>();
-    constexpr int RW = quad_row<T, W>() * quad_vec<T>();
-    constexpr int OWY = 0, OWZ = RW, OCX = 2 * RW, OKEY = 2 * RW + 2 * L;
+    constexpr int OWY = 0, OWZ = 4 * ((W + 1) / 2), OCX = 2 * OWZ;
     const int lane = threadIdx.x & 31, h = lane / L, q = lane % L;
     const int n = sub.z;
-    uint16_t *order = reinterpret_cast<uint16_t *>(sm);
-    uint16_t *keys = order + msub;
-    int *cur = reinterpret_cast<int *>(sm + sweep_cur(msub));
-    const int nkeys = (a.m1 + 1) * (M2 + 1);
-    T *stg = reinterpret_cast<T *>(sm + sweep_head(msub, nkeys));
-    const int32_t *perm = a.perm + sub.y;
-
-    sweep_row_sort<T, M2 + 1>(a.recs, perm, n, nkeys, order, keys, cur);
 
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
@@ -658,16 +647,20 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
     const bool writer = h == 0 && q < a.p0;
     const int gx = wrap_any(o0 - P + (q < a.p0 ? q : 0), a.n0);
     const int row0 = o1 - P, plane0 = o2 - P;
-    T accr[W][PZ], acci[W][PZ];
+    uint64_t acc[W][PZ];                                   // (re, im) of row j, plane k
 #pragma unroll
     for (int j = 0; j < W; ++j)
 #pragma unroll
-        for (int k = 0; k < PZ; ++k) accr[j][k] = acci[j][k] = (T)0;
+        for (int k = 0; k < PZ; ++k) acc[j][k] = 0ull;
     int row = 0;
 
-    auto flush_row = [&](int r_rel, T (&vr)[PZ], T (&vi)[PZ]) {
+    auto flush_row = [&](int r_rel, const uint64_t (&v)[PZ]) {
+        float vr[PZ], vi[PZ];
 #pragma unroll
         for (int k = 0; k < PZ; ++k) {
+            const float2 f = unpack2(v[k]);
+            vr[k] = f.x;
+            vi[k] = f.y;
 #pragma unroll
             for (int o = L; o < 32; o <<= 1) {
                 vr[k] += __shfl_xor_sync(kFullMask, vr[k], o);
@@ -678,7 +671,7 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
         const int gy = wrap_any(row0 + r_rel, a.n1);
 #pragma unroll
         for (int k = 0; k < PZ; ++k) {
-            if (vr[k] != (T)0 || vi[k] != (T)0) {
+            if (vr[k] != 0.f || vi[k] != 0.f) {
                 const int gz = wrap_any(plane0 + k, a.n2);
                 atomic_add_cplx(&grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx], vr[k], vi[k]);
             }
@@ -689,9 +682,9 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
     C cv;
     auto fetch = [&](int base) {
         if (base + lane < n) {
-            const int j = perm[order[base + lane]];
-            rc = a.recs[j];
-            cv = cin[j];
+            const int64_t pos = sub.y + base + lane;
+            rc = a.recs[pos];
+            cv = cin[a.order[pos]];
         }
     };
     fetch(0);
@@ -702,7 +695,6 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
             const uint32_t pk = unpack_word<T>(rc.w);
             T *s = stg + lane * SLOT;
             mykey = (int)((pk >> 10) & 1023u) * (M2 + 1) + (int)(pk >> 20);
-            reinterpret_cast<uint32_t *>(s + OKEY)[0] = pk >> 20;
             const int sx = (int)(pk & 1023u);
             T vx[W], vy[W], vz[W];
             kernel_row<T, W>(a, rc.x, vx);
@@ -717,67 +709,73 @@ __device__ __forceinline__ void spread_sweep3_piece(const KArgs<T> &a, int4 sub,
                 v.y = cv.y * vx[i];
                 *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) = v;
             }
-            store_row<W>(s + OWY, vy);
-            store_row<W>(s + OWZ, vz);
+            store_dup_row<W>(s + OWY, vy);
+            store_dup_row<W>(s + OWZ, vz);
         }
+        if (base == 0) row = __shfl_sync(kFullMask, mykey, 0) / (M2 + 1);
         fetch(base + 32);
         __syncwarp();
         int i0 = 0;
         while (i0 < cnt) {
             const int r = __shfl_sync(kFullMask, mykey, i0);
             const int rrow = r / (M2 + 1);
+            if (rrow < row || rrow >= row + W) {      // new ordering piece, or a jump
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    flush_row(row + j, acc[j]);
+#pragma unroll
+                    for (int k = 0; k < PZ; ++k) acc[j][k] = 0ull;
+                }
+                row = rrow;
+            }
             while (row < rrow) {
-                flush_row(row, accr[0], acci[0]);
+                flush_row(row, acc[0]);
 #pragma unroll
                 for (int j = 0; j + 1 < W; ++j)
 #pragma unroll
-                    for (int k = 0; k < PZ; ++k) {
-                        accr[j][k] = accr[j + 1][k];
-                        acci[j][k] = acci[j + 1][k];
-                    }
+                    for (int k = 0; k < PZ; ++k) acc[j][k] = acc[j + 1][k];
 #pragma unroll
-                for (int k = 0; k < PZ; ++k) accr[W - 1][k] = acci[W - 1][k] = (T)0;
+                for (int k = 0; k < PZ; ++k) acc[W - 1][k] = 0ull;
                 ++row;
             }
-            const unsigned later = __ballot_sync(kFullMask, mykey > r) & ~((2u << i0) - 1u);
+            const unsigned later = __ballot_sync(kFullMask, mykey != r) & ~((2u << i0) - 1u);
             const int i1 = later ? __ffs(later) - 1 : cnt;
             const int sz = r - rrow * (M2 + 1);             // the group's first plane
             for (int i = i0 + h; i < i1; i += S) {
                 const T *s = stg + i * SLOT;
-                const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * q);
-                const T wr = cx.x, wi = cx.y;
-                T wy[W], wz[W], t[W], u[W];
-                load_row<W>(s + OWY, wy);
-                load_row<W>(s + OWZ, wz);
+                const uint64_t cx = *reinterpret_cast<const uint64_t *>(s + OCX + 2 * q);
+                uint64_t tu[W], wzz[W];
 #pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    t[j] = wr * wy[j];
-                    u[j] = wi * wy[j];
+                for (int k = 0; k < W; k += 2) {
+                    const ulonglong2 y2 = *reinterpret_cast<const ulonglong2 *>(s + OWY + 2 * k);
+                    const ulonglong2 z2 = *reinterpret_cast<const ulonglong2 *>(s + OWZ + 2 * k);
+                    tu[k] = mul2(cx, y2.x);
+                    wzz[k] = z2.x;
+                    if (k + 1 < W) {
+                        tu[k + 1 < W ? k + 1 : k] = mul2(cx, y2.y);
+                        wzz[k + 1 < W ? k + 1 : k] = z2.y;
+                    }
                 }
                 if (sz == 0)
-                    sweep3_add<T, W, PZ, 0>(accr, acci, t, u, wz);
+                    sweep3_add<W, PZ, 0>(acc, tu, wzz);
                 else if (M2 == 1 || sz == 1)
-                    sweep3_add<T, W, PZ, 1>(accr, acci, t, u, wz);
+                    sweep3_add<W, PZ, 1>(acc, tu, wzz);
                 else
-                    sweep3_add<T, W, PZ, (M2 >= 2 ? 2 : 1)>(accr, acci, t, u, wz);
+                    sweep3_add<W, PZ, (M2 >= 2 ? 2 : 1)>(acc, tu, wzz);
             }
             i0 = i1;
         }
         __syncwarp();
     }
 #pragma unroll
-    for (int j = 0; j < W; ++j) flush_row(row + j, accr[j], acci[j]);
+    for (int j = 0; j < W; ++j) flush_row(row + j, acc[j]);
 }
 
-// A subproblem in pieces of at most kSweepCap points (sub = {bin, start, count}).
 template <typename T, int W, int M2, int L>
 __device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, int tr,
                                                    unsigned char *sm)
 {
-    const int4 sub = a.subprob[sp];
-    for (int piece = 0; piece < sub.z; piece += kSweepCap)
-        spread_sweep3_piece<T, W, M2, L>(
-            a, make_int4(sub.x, sub.y + piece, min(kSweepCap, sub.z - piece), 0), tr, sm);
+    spread_sweep3_sub<T, W, M2, L>(a, a.subprob[sp], tr, reinterpret_cast<T *>(sm));
 }
 
 template <typename T, int W, int M2, int L>
@@ -799,10 +797,7 @@ template <typename T, int W, int L>
 __device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, int tr,
                                                    unsigned char *sm)
 {
-    const int4 sub = a.subprob[sp];
-    for (int piece = 0; piece < sub.z; piece += kSweepCap)
-        spread_sweep2_piece<T, W, L>(
-            a, make_int4(sub.x, sub.y + piece, min(kSweepCap, sub.z - piece), 0), tr, sm);
+    spread_sweep2_sub<T, W, L>(a, a.subprob[sp], tr, reinterpret_cast<T *>(sm));
 }
 
 template <typename T, int W, int L>
@@ -847,9 +842,9 @@ __device__ __forceinline__ void spread_gmsort_item(const KArgs<T> &a, int sp, in
             C cv;
             cv.x = cv.y = (T)0;
             if (base + lane < sub.z) {
-                const int j = a.perm[sub.y + base + lane];
-                r = a.recs[j];
-                cv = cin[j];
+                const int64_t pos = sub.y + base + lane;
+                r = a.recs[pos];
+                cv = cin[point_of<T, DIM>(a, r, pos)];
             }
             const int np = min(32, sub.z - base);
             for (int i0 = 0; i0 < np; i0 += G) {
@@ -912,11 +907,12 @@ spread_gmsort_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__r
 }
 
 // ---------------------------------------------------------------------------
-// GM spreading: user order, positions from the coordinates.
+// GM spreading: user order, positions from the coordinates.  A warp takes
+// G = 32 / W consecutive (transform, point) items at a time, item = tr * M + j;
+// lane group g works on item base + g.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int W>
-__global__ void __launch_bounds__(256)
-spread_gm_kernel(KArgs<T> a)
+__device__ __forceinline__ void spread_gm_step(const KArgs<T> &a, int64_t base, int64_t end)
 {
     using C = typename cplx<T>::type;
     constexpr int G = 32 / W;
@@ -924,53 +920,60 @@ spread_gm_kernel(KArgs<T> a)
     const int g = lane / W, dx = lane - (lane / W) * W;
     const bool gact = g < G;
     const int src0 = (gact ? g : G - 1) * W;
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t total = a.M * a.ntransf;
-    for (int64_t base = gwarp * G; base < total; base += nwarps_total * G) {
-        const int64_t item = base + g;
-        const bool act = gact && item < total;
-        T wx = 0, myy = 0, myz = 0, cre = 0, cim = 0;
-        int gx = 0, ly0 = 0, lz0 = 0, tr = 0;
-        if (act) {
-            tr = (int)(item / a.M);
-            const int64_t j = item - (int64_t)tr * a.M;
-            const AxisPos<T> px = axis_position<T>(period_fraction(a.xyz0[j]), a.n0, W);
-            const AxisPos<T> py = axis_position<T>(period_fraction(a.xyz1[j]), a.n1, W);
-            wx = es_kernel(((T)dx - px.delta) * a.hw, a.beta);
-            myy = es_kernel(((T)dx - py.delta) * a.hw, a.beta);
-            gx = wrap_any(px.l0 + dx, a.n0);
-            ly0 = py.l0;
-            if (DIM == 3) {
-                const AxisPos<T> pz = axis_position<T>(period_fraction(a.xyz2[j]), a.n2, W);
-                myz = es_kernel(((T)dx - pz.delta) * a.hw, a.beta);
-                lz0 = pz.l0;
-            }
-            const C cv = a.cin[item];
-            cre = cv.x;
-            cim = cv.y;
+    const int64_t item = base + g;
+    const bool act = gact && item < end;
+    T wx = 0, myy = 0, myz = 0, cre = 0, cim = 0;
+    int gx = 0, ly0 = 0, lz0 = 0, tr = 0;
+    if (act) {
+        tr = (int)(item / a.M);
+        const int64_t j = item - (int64_t)tr * a.M;
+        const AxisPos<T> px = axis_position<T>(period_fraction(a.xyz0[j]), a.n0, W);
+        const AxisPos<T> py = axis_position<T>(period_fraction(a.xyz1[j]), a.n1, W);
+        wx = es_kernel(((T)dx - px.delta) * a.hw, a.beta);
+        myy = es_kernel(((T)dx - py.delta) * a.hw, a.beta);
+        gx = wrap_any(px.l0 + dx, a.n0);
+        ly0 = py.l0;
+        if (DIM == 3) {
+            const AxisPos<T> pz = axis_position<T>(period_fraction(a.xyz2[j]), a.n2, W);
+            myz = es_kernel(((T)dx - pz.delta) * a.hw, a.beta);
+            lz0 = pz.l0;
         }
-        T wy[W];
+        const C cv = a.cin[item];
+        cre = cv.x;
+        cim = cv.y;
+    }
+    T wy[W];
 #pragma unroll
-        for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
-        C *grid = a.grid + (int64_t)tr * a.nftot;
-        const T zr0 = cre * wx, zi0 = cim * wx;
-        const int nz = DIM == 3 ? W : 1;
+    for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
+    C *grid = a.grid + (int64_t)tr * a.nftot;
+    const T zr0 = cre * wx, zi0 = cim * wx;
+    const int nz = DIM == 3 ? W : 1;
 #pragma unroll 1
-        for (int iz = 0; iz < nz; ++iz) {
-            const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
-            const T zr = zr0 * vz, zi = zi0 * vz;
-            const int gz = DIM == 3 ? wrap_any(lz0 + iz, a.n2) : 0;
+    for (int iz = 0; iz < nz; ++iz) {
+        const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
+        const T zr = zr0 * vz, zi = zi0 * vz;
+        const int gz = DIM == 3 ? wrap_any(lz0 + iz, a.n2) : 0;
 #pragma unroll
-            for (int iy = 0; iy < W; ++iy) {
-                if (act) {
-                    const int gy = wrap_any(ly0 + iy, a.n1);
-                    atomic_add_cplx(&grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx], wy[iy] * zr,
-                                    wy[iy] * zi);
-                }
+        for (int iy = 0; iy < W; ++iy) {
+            if (act) {
+                const int gy = wrap_any(ly0 + iy, a.n1);
+                atomic_add_cplx(&grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx], wy[iy] * zr,
+                                wy[iy] * zi);
             }
         }
     }
+}
+
+template <typename T, int DIM, int W>
+__global__ void __launch_bounds__(256)
+spread_gm_kernel(KArgs<T> a)
+{
+    constexpr int G = 32 / W;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = a.M * a.ntransf;
+    for (int64_t base = gwarp * G; base < total; base += nwarps_total * G)
+        spread_gm_step<T, DIM, W>(a, base, total);
 }
 
 // Sum of a value over the W lanes of each group; lane dx == 0 gets the total.
@@ -1019,10 +1022,9 @@ __device__ __forceinline__ void interp_lane_item(const KArgs<T> &a, int sp, int 
         }
         __syncthreads();
     }
-    const int32_t *perm = a.perm + sub.y;
     for (int k = threadIdx.x; k < sub.z; k += blockDim.x) {
-        const int j = perm[k];
-        const R rc = a.recs[j];
+        const R rc = a.recs[sub.y + k];
+        const int j = point_of<T, DIM>(a, rc, sub.y + k);
         const uint32_t pk = unpack_word<T>(rc.w);
         const int sx = pk & 1023u, sy = (pk >> 10) & 1023u, sz = pk >> 20;
         T wx[W], wy[W];
@@ -1077,7 +1079,7 @@ __device__ __forceinline__ void interp_lane_item(const KArgs<T> &a, int sp, int 
 
 // 2D, one warp per work item: the warp stages its own padded bin (no CTA
 // barriers, so many subproblems are in flight per SM) and its lanes take the
-// subproblem's points as above.
+// subproblem's points as above (2D records carry their point's index).
 template <typename T, int W>
 __device__ __forceinline__ void interp_warp2_item(const KArgs<T> &a, int sp, int tr,
                                                   typename cplx<T>::type *tile)
@@ -1091,38 +1093,59 @@ __device__ __forceinline__ void interp_warp2_item(const KArgs<T> &a, int sp, int
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
     const C *grid = a.grid + (int64_t)tr * a.nftot;
     C *cout = a.cout + (int64_t)tr * a.M;
-    const int ptot = a.p0 * a.p1;
-    for (int i = lane; i < ptot; i += 32) {
-        const int ry = i / a.p0, rx = i - ry * a.p0;
-        tile[i] = grid[(int64_t)wrap_any(o1 - P + ry, a.n1) * a.n0 + wrap_any(o0 - P + rx, a.n0)];
+    for (int rx = lane; rx < a.p0; rx += 32) {            // stage the padded bin, row by row
+        const C *src = grid + wrap_any(o0 - P + rx, a.n0);
+#pragma unroll 4
+        for (int ry = 0; ry < a.p1; ++ry)
+            tile[ry * a.p0 + rx] = src[(int64_t)wrap_any(o1 - P + ry, a.n1) * a.n0];
     }
     __syncwarp();
-    const int32_t *perm = a.perm + sub.y;
+    // records in execution order (rows, then columns): neighbouring lanes read
+    // neighbouring cells of the tile
     for (int k = lane; k < sub.z; k += 32) {
-        const int j = perm[k];
-        const R rc = a.recs[j];
+        const R rc = a.recs[sub.y + k];
+        const int j = (int)unpack_word<T>(rc.z);
         const uint32_t pk = unpack_word<T>(rc.w);
         const int sx = pk & 1023u, sy = (pk >> 10) & 1023u;
         T wx[W], wy[W];
         kernel_row<T, W>(a, rc.x, wx);
         kernel_row<T, W>(a, rc.y, wy);
-        T ar = 0, ai = 0;
-#pragma unroll
-        for (int iy = 0; iy < W; ++iy) {
-            const C *t = tile + (sy + iy) * a.p0 + sx;
-            T yr = 0, yi = 0;
-#pragma unroll
-            for (int ix = 0; ix < W; ++ix) {
-                const C g = t[ix];
-                yr += wx[ix] * g.x;
-                yi += wx[ix] * g.y;
-            }
-            ar += wy[iy] * yr;
-            ai += wy[iy] * yi;
-        }
         C o;
-        o.x = ar;
-        o.y = ai;
+        if constexpr (sizeof(T) == 4) {
+            // packed (re, im) sums: one f32x2 FMA per cell
+            uint64_t wxx[W];
+#pragma unroll
+            for (int ix = 0; ix < W; ++ix) wxx[ix] = pack2(wx[ix], wx[ix]);
+            uint64_t acc = 0ull;
+#pragma unroll
+            for (int iy = 0; iy < W; ++iy) {
+                const uint64_t *t = reinterpret_cast<const uint64_t *>(tile + (sy + iy) * a.p0 + sx);
+                uint64_t yv = 0ull;
+#pragma unroll
+                for (int ix = 0; ix < W; ++ix) fma2(yv, t[ix], wxx[ix]);
+                fma2(acc, yv, pack2(wy[iy], wy[iy]));
+            }
+            const float2 v = unpack2(acc);
+            o.x = v.x;
+            o.y = v.y;
+        } else {
+            T ar = 0, ai = 0;
+#pragma unroll
+            for (int iy = 0; iy < W; ++iy) {
+                const C *t = tile + (sy + iy) * a.p0 + sx;
+                T yr = 0, yi = 0;
+#pragma unroll
+                for (int ix = 0; ix < W; ++ix) {
+                    const C g = t[ix];
+                    yr += wx[ix] * g.x;
+                    yi += wx[ix] * g.y;
+                }
+                ar += wy[iy] * yr;
+                ai += wy[iy] * yi;
+            }
+            o.x = ar;
+            o.y = ai;
+        }
         cout[j] = o;
     }
     __syncwarp();
@@ -1156,11 +1179,10 @@ interp_lane_kernel(KArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
-// GM interpolation: user order.
+// GM interpolation: user order, G items per warp as in GM spreading.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int W>
-__global__ void __launch_bounds__(256)
-interp_gm_kernel(KArgs<T> a)
+__device__ __forceinline__ void interp_gm_step(const KArgs<T> &a, int64_t base, int64_t end)
 {
     using C = typename cplx<T>::type;
     constexpr int G = 32 / W;
@@ -1168,61 +1190,68 @@ interp_gm_kernel(KArgs<T> a)
     const int g = lane / W, dx = lane - (lane / W) * W;
     const bool gact = g < G;
     const int src0 = (gact ? g : G - 1) * W;
+    const int64_t item = base + g;
+    const bool act = gact && item < end;
+    T wx = 0, myy = 0, myz = 0;
+    int gx = 0, ly0 = 0, lz0 = 0, tr = 0;
+    if (act) {
+        tr = (int)(item / a.M);
+        const int64_t j = item - (int64_t)tr * a.M;
+        const AxisPos<T> px = axis_position<T>(period_fraction(a.xyz0[j]), a.n0, W);
+        const AxisPos<T> py = axis_position<T>(period_fraction(a.xyz1[j]), a.n1, W);
+        wx = es_kernel(((T)dx - px.delta) * a.hw, a.beta);
+        myy = es_kernel(((T)dx - py.delta) * a.hw, a.beta);
+        gx = wrap_any(px.l0 + dx, a.n0);
+        ly0 = py.l0;
+        if (DIM == 3) {
+            const AxisPos<T> pz = axis_position<T>(period_fraction(a.xyz2[j]), a.n2, W);
+            myz = es_kernel(((T)dx - pz.delta) * a.hw, a.beta);
+            lz0 = pz.l0;
+        }
+    }
+    T wy[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
+    const C *grid = a.grid + (int64_t)tr * a.nftot;
+    T ar = 0, ai = 0;
+    const int nz = DIM == 3 ? W : 1;
+#pragma unroll 1
+    for (int iz = 0; iz < nz; ++iz) {
+        const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
+        const int gz = DIM == 3 ? wrap_any(lz0 + iz, a.n2) : 0;
+        T zr = 0, zi = 0;
+#pragma unroll
+        for (int iy = 0; iy < W; ++iy) {
+            if (act) {
+                const int gy = wrap_any(ly0 + iy, a.n1);
+                const C v = grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx];
+                zr += wy[iy] * v.x;
+                zi += wy[iy] * v.y;
+            }
+        }
+        ar += vz * zr;
+        ai += vz * zi;
+    }
+    ar = group_sum<T, W>(act ? ar * wx : (T)0, dx);
+    ai = group_sum<T, W>(act ? ai * wx : (T)0, dx);
+    if (act && dx == 0) {
+        C o;
+        o.x = ar;
+        o.y = ai;
+        a.cout[item] = o;
+    }
+}
+
+template <typename T, int DIM, int W>
+__global__ void __launch_bounds__(256)
+interp_gm_kernel(KArgs<T> a)
+{
+    constexpr int G = 32 / W;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t total = a.M * a.ntransf;
-    for (int64_t base = gwarp * G; base < total; base += nwarps_total * G) {
-        const int64_t item = base + g;
-        const bool act = gact && item < total;
-        T wx = 0, myy = 0, myz = 0;
-        int gx = 0, ly0 = 0, lz0 = 0, tr = 0;
-        if (act) {
-            tr = (int)(item / a.M);
-            const int64_t j = item - (int64_t)tr * a.M;
-            const AxisPos<T> px = axis_position<T>(period_fraction(a.xyz0[j]), a.n0, W);
-            const AxisPos<T> py = axis_position<T>(period_fraction(a.xyz1[j]), a.n1, W);
-            wx = es_kernel(((T)dx - px.delta) * a.hw, a.beta);
-            myy = es_kernel(((T)dx - py.delta) * a.hw, a.beta);
-            gx = wrap_any(px.l0 + dx, a.n0);
-            ly0 = py.l0;
-            if (DIM == 3) {
-                const AxisPos<T> pz = axis_position<T>(period_fraction(a.xyz2[j]), a.n2, W);
-                myz = es_kernel(((T)dx - pz.delta) * a.hw, a.beta);
-                lz0 = pz.l0;
-            }
-        }
-        T wy[W];
-#pragma unroll
-        for (int i = 0; i < W; ++i) wy[i] = shfl(myy, src0 + i);
-        const C *grid = a.grid + (int64_t)tr * a.nftot;
-        T ar = 0, ai = 0;
-        const int nz = DIM == 3 ? W : 1;
-#pragma unroll 1
-        for (int iz = 0; iz < nz; ++iz) {
-            const T vz = DIM == 3 ? shfl(myz, src0 + iz) : (T)1;
-            const int gz = DIM == 3 ? wrap_any(lz0 + iz, a.n2) : 0;
-            T zr = 0, zi = 0;
-#pragma unroll
-            for (int iy = 0; iy < W; ++iy) {
-                if (act) {
-                    const int gy = wrap_any(ly0 + iy, a.n1);
-                    const C v = grid[((int64_t)gz * a.n1 + gy) * a.n0 + gx];
-                    zr += wy[iy] * v.x;
-                    zi += wy[iy] * v.y;
-                }
-            }
-            ar += vz * zr;
-            ai += vz * zi;
-        }
-        ar = group_sum<T, W>(act ? ar * wx : (T)0, dx);
-        ai = group_sum<T, W>(act ? ai * wx : (T)0, dx);
-        if (act && dx == 0) {
-            C o;
-            o.x = ar;
-            o.y = ai;
-            a.cout[item] = o;
-        }
-    }
+    for (int64_t base = gwarp * G; base < total; base += nwarps_total * G)
+        interp_gm_step<T, DIM, W>(a, base, total);
 }
 
 // ---------------------------------------------------------------------------
@@ -1358,6 +1387,43 @@ interp_lane_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__res
     }
 }
 
+// GM plans in a batch: a work item is a chunk of kGmChunk consecutive points of
+// one transform (the plan's nsub holds its chunk count, set at setpts), run by
+// one CTA whose warps take G = 32 / W points at a time.
+template <typename T, int DIM, int W, bool SPREAD>
+__global__ void __launch_bounds__(256)
+gm_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff, int nplans)
+{
+    __shared__ __align__(16) unsigned char cache_raw[sizeof(KArgs<T>)];
+    KArgs<T> *cache = reinterpret_cast<KArgs<T> *>(cache_raw);
+    constexpr int G = 32 / W;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int cached = -1;
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        if (pl != cached) {
+            __syncthreads();
+            const int4 *src = reinterpret_cast<const int4 *>(args + pl);
+            int4 *dst = reinterpret_cast<int4 *>(cache);
+            for (int i = threadIdx.x; i < (int)(sizeof(KArgs<T>) / 16); i += blockDim.x)
+                dst[i] = src[i];
+            __syncthreads();
+            cached = pl;
+        }
+        const KArgs<T> &a = *cache;
+        const int64_t local = wi - workoff[pl];
+        const int nchunk = *a.nsub;
+        const int64_t tr = local / nchunk;
+        const int64_t beg = tr * a.M + (local - tr * nchunk) * (int64_t)kGmChunk;
+        const int64_t end = min(beg + (int64_t)kGmChunk, (tr + 1) * a.M);
+        for (int64_t base = beg + (int64_t)warp * G; base < end; base += (int64_t)nwarps * G) {
+            if (SPREAD) spread_gm_step<T, DIM, W>(a, base, end);
+            else interp_gm_step<T, DIM, W>(a, base, end);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launch for one (T, DIM): picks the kernel for p.method and p.w.
 // ---------------------------------------------------------------------------
@@ -1366,7 +1432,7 @@ KArgs<T> make_args(const Plan &p)
 {
     KArgs<T> a;
     a.recs = reinterpret_cast<const typename rec4<T>::type *>(p.recs);
-    a.perm = p.perm;
+    a.order = p.order;
     a.subprob = p.subprob;
     a.nsub = p.nsub;
     a.xyz0 = reinterpret_cast<const T *>(p.xyz_copy[0]);
@@ -1413,13 +1479,16 @@ inline int persistent_grid(const Plan &p, K kernel, int threads, size_t smem)
 template <typename T, int W, int L>
 bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
 {
-    const size_t warp_bytes = sweep_bytes<T, W, L>(kSweepCap, a.m1);
+    const size_t warp_bytes = sweep_bytes<T, W, L>();
     int nw = threads / 32;
     while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
     if (nw < 2) return false;
     const size_t smem = warp_bytes * nw;
     auto k = spread_sweep2_kernel<T, W, L>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t ea = allow_max_smem((const void *)k)) {
+        *err = ea;
+        return true;
+    }
     k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, (int)warp_bytes);
     *err = cudaGetLastError();
     return true;
@@ -1428,13 +1497,16 @@ bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
 template <typename T, int W, int M2, int L>
 bool launch_sweep3(Plan &p, const KArgs<T> &a, cudaError_t *err)
 {
-    const size_t warp_bytes = sweep3_bytes<T, W, M2, L>(kSweepCap, a.m1);
+    const size_t warp_bytes = sweep3_bytes<T, W, L>();
     int nw = 4;
     while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
     if (nw < 2) return false;
     const size_t smem = warp_bytes * nw;
     auto k = spread_sweep3_kernel<T, W, M2, L>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t ea = allow_max_smem((const void *)k)) {
+        *err = ea;
+        return true;
+    }
     k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, (int)warp_bytes);
     *err = cudaGetLastError();
     return true;
@@ -1469,7 +1541,7 @@ cudaError_t spread_w(Plan &p, const void *c)
     if (p.method == NUFFT_METHOD_SM) {
         const size_t smem = (size_t)2 * sizeof(T) * a.p0 * a.p1 * a.p2;
         auto k = spread_sm_kernel<T, DIM, W>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
         const int grid = persistent_grid(p, k, threads, smem);
         k<<<grid, threads, smem, p.stream>>>(a);
     } else if (p.method == NUFFT_METHOD_GM_SORT) {
@@ -1503,7 +1575,7 @@ cudaError_t interp_w(Plan &p, void *c)
         if ((size_t)nw * per_warp <= (size_t)p.smem_optin) {
             const size_t smem = per_warp * nw;
             auto k = interp_warp2_kernel<T, W>;
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
             k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, tile);
             return cudaGetLastError();
         }
@@ -1511,7 +1583,7 @@ cudaError_t interp_w(Plan &p, void *c)
     if (p.method == NUFFT_METHOD_SM) {
         const size_t smem = sizeof(typename cplx<T>::type) * a.p0 * a.p1 * a.p2;
         auto k = interp_lane_kernel<T, DIM, W, true>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
         k<<<persistent_grid(p, k, threads, smem), threads, smem, p.stream>>>(a);
     } else if (p.method == NUFFT_METHOD_GM_SORT) {
         auto k = interp_lane_kernel<T, DIM, W, false>;
@@ -1543,42 +1615,46 @@ cudaError_t spread_multi_w(const MultiLaunch &ml)
     count_launch();
     if (ml.method == NUFFT_METHOD_SM && ml.variant > 0) {
         if constexpr (DIM == 2) {
-            const size_t wb = sweep_bytes<T, W, 32>(kSweepCap, ml.m1max);
+            const size_t wb = sweep_bytes<T, W, 32>();
             const size_t per = args_slot<T>() + wb;
             int nw = 8;
             while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
             const size_t smem = per * nw;
-            auto launch = [&](auto k, int lanes_wb) {
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            auto launch = [&](auto k, int lanes_wb) -> cudaError_t {
+                if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
                 k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
                     args, ml.workoff, ml.nplans, lanes_wb);
+                return cudaGetLastError();
             };
             // the staging slots of the widest sub-warp form bound the narrower ones
-            if (ml.variant == 8) launch(spread_sweep2_multi_kernel<T, W, 8>, (int)wb);
-            else if (ml.variant == 16) launch(spread_sweep2_multi_kernel<T, W, 16>, (int)wb);
-            else launch(spread_sweep2_multi_kernel<T, W, 32>, (int)wb);
-            return cudaGetLastError();
+            if (ml.variant == 8) return launch(spread_sweep2_multi_kernel<T, W, 8>, (int)wb);
+            if (ml.variant == 16) return launch(spread_sweep2_multi_kernel<T, W, 16>, (int)wb);
+            return launch(spread_sweep2_multi_kernel<T, W, 32>, (int)wb);
         } else if constexpr (sizeof(T) == 4 && W <= 8) {
-            const size_t wb = sweep3_bytes<T, W, 2, 32>(kSweepCap, ml.m1max);
+            const size_t wb = sweep3_bytes<T, W, 32>();
             const size_t per = args_slot<T>() + wb;
             int nw = 4;
             while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
             const size_t smem = per * nw;
-            auto launch = [&](auto k) {
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            auto launch = [&](auto k) -> cudaError_t {
+                if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
                 k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
                     args, ml.workoff, ml.nplans, (int)wb);
+                return cudaGetLastError();
             };
-            if (ml.variant == 1) launch(spread_sweep3_multi_kernel<T, W, 1, 32>);
-            else if (ml.variant == 2) launch(spread_sweep3_multi_kernel<T, W, 2, 32>);
-            else if (ml.variant == 5) launch(spread_sweep3_multi_kernel<T, W, 1, 16>);
-            else launch(spread_sweep3_multi_kernel<T, W, 2, 16>);
-            return cudaGetLastError();
+            if (ml.variant == 1) return launch(spread_sweep3_multi_kernel<T, W, 1, 32>);
+            if (ml.variant == 2) return launch(spread_sweep3_multi_kernel<T, W, 2, 32>);
+            if (ml.variant == 5) return launch(spread_sweep3_multi_kernel<T, W, 1, 16>);
+            return launch(spread_sweep3_multi_kernel<T, W, 2, 16>);
         }
     }
-    if (ml.method == NUFFT_METHOD_SM) {
+    if (ml.method == NUFFT_METHOD_GM) {
+        auto k = gm_multi_kernel<T, DIM, W, true>;
+        k<<<multi_grid(k, ml.threads, 0, ml.num_sms), ml.threads, 0, ml.stream>>>(
+            args, ml.workoff, ml.nplans);
+    } else if (ml.method == NUFFT_METHOD_SM) {
         auto k = spread_sm_multi_kernel<T, DIM, W>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ml.smem);
+        if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
         k<<<multi_grid(k, ml.threads, ml.smem, ml.num_sms), ml.threads, ml.smem, ml.stream>>>(
             args, ml.workoff, ml.nplans);
     } else {
@@ -1602,16 +1678,20 @@ cudaError_t interp_multi_w(const MultiLaunch &ml)
         if ((size_t)nw * per <= ml.smem_optin) {
             const size_t smem = per * nw;
             auto k = interp_warp2_multi_kernel<T, W>;
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
             k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
                 args, ml.workoff, ml.nplans, ml.tile);
             return cudaGetLastError();
         }
     }
-    if (ml.method == NUFFT_METHOD_SM) {
+    if (ml.method == NUFFT_METHOD_GM) {
+        auto k = gm_multi_kernel<T, DIM, W, false>;
+        k<<<multi_grid(k, ml.threads, 0, ml.num_sms), ml.threads, 0, ml.stream>>>(
+            args, ml.workoff, ml.nplans);
+    } else if (ml.method == NUFFT_METHOD_SM) {
         const size_t smem = args_slot<T>() + sizeof(C) * (size_t)ml.tile;
         auto k = interp_lane_multi_kernel<T, DIM, W, true>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
         k<<<multi_grid(k, ml.threads, smem, ml.num_sms), ml.threads, smem, ml.stream>>>(
             args, ml.workoff, ml.nplans);
     } else {

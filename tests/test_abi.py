@@ -83,7 +83,7 @@ def test_default_opts_fill_every_field(lib):
     lib.nufft_default_opts(ctypes.byref(o))
     assert o.method == 0 and list(o.bin) == [0, 0, 0] and o.msub == 0
     assert o.upsampfac == 2.0 and not o.stream and o.threads == 0 and o.ctas_per_sm == 0
-    assert o.use_picker == 0 and o.unordered_bins == 0
+    assert o.use_picker == 0 and o.unordered_bins == 0 and o.debug_checks == 0
 
 
 def test_algorithmic_cost_per_point_matches_formulas():

@@ -3,10 +3,12 @@
 For each workload the GPU result is compared
   * with the oracle's FP64 three-step pipeline at the same kernel width on ALL
     outputs (only rounding differs: bound TOL_SAME_W below), and
-  * with the exact sums (oracle O1) on sampled modes / targets: relative l2 over
-    the sample <= max(2 eps, oracle pipeline's own sampled error + slack).
+  * with the exact sums (oracle O1) on sampled modes / targets: relative l2
+    over the sample <= 2 eps, or, where the FP64 pipeline at the same width
+    itself misses 2 eps on that sample, <= its error + 0.2 eps (the GPU's
+    rounding adds in quadrature to the method's error).
 Inputs are the seeded synthetic workloads of bench.py (SplitMix64 points and
-N(0,1) strengths / modes).
+N(0,1) strengths / modes); "cluster" is the paper's box [0, 8h]^d (Sec. 5).
 """
 import numpy as np
 import pytest
@@ -18,7 +20,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-NSAMP = 32
+NSAMP = 64
 # Rounding bound GPU vs FP64 pipeline at the same w: single precision carries
 # ~1e-7 relative error per kernel value (amplified by up to beta ~ 16 through
 # the exponent), per accumulated term and per cuFFT stage; 1e-5 covers w <= 7.
@@ -70,8 +72,13 @@ def _check(type_, N, eps, prec, pts, data, got, w, seed):
     e_same = oracle.rel_l2(got, same_w)
     e_exact = oracle.rel_l2(got_s, exact)
     e_oracle = oracle.rel_l2(same_s, exact)
+    bar = max(2 * eps, e_oracle + 0.2 * eps)
+    from conftest import record_exact_error
+    record_exact_error("fullsize type%d N=%s eps=%g (%d sampled)" % (type_, "x".join(map(str, N)),
+                                                                   eps, NSAMP),
+                       eps, e_exact, e_oracle, bar)
     assert e_same < TOL_SAME_W[prec], e_same
-    assert e_exact <= max(2 * eps, e_oracle + 2 * TOL_SAME_W[prec]), (e_exact, e_oracle)
+    assert e_exact <= bar, (e_exact, e_oracle, bar)
     return e_same, e_exact, e_oracle
 
 
@@ -84,7 +91,8 @@ def test_2d_1024_fullsize(nb, type_, eps, prec):
 
 
 @pytest.mark.parametrize("type_", [1, 2])
-@pytest.mark.parametrize("kind,eps", [("rand", 1e-2), ("rand", 1e-6), ("gauss", 1e-6)])
+@pytest.mark.parametrize("kind,eps", [("rand", 1e-2), ("rand", 1e-6), ("gauss", 1e-2),
+                                      ("gauss", 1e-6), ("cluster", 1e-2), ("cluster", 1e-6)])
 def test_3d_128_fullsize(nb, type_, kind, eps):
     N, M, seed = (128, 128, 128), 16777216, 9200
     pts, data, got, w = _run(nb, type_, 3, N, M, eps, 0, kind, seed)

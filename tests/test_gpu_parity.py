@@ -8,9 +8,13 @@ Three bars, each stated where it is used:
     only differences are rounding: relative l2 <= 2e-5 in single precision,
     <= 1e-11 in double (a few ulps of the working precision times the
     conditioning of the sums over w^d kernel values and the FFT);
-  * against the exact sums, relative l2 <= 2 eps where the oracle pipeline at
-    that width meets eps (the width rule of Sec. 3), else <= oracle error plus
-    the rounding allowance.
+  * against the exact sums, relative l2 <= 2 eps; where the FP64 oracle
+    pipeline at the same width itself misses 2 eps (the width rule of Sec. 3 is
+    an empirical one, and at w = 10, 13 it lands at 2-3.7 eps), at most that
+    error plus 0.2 eps.  The allowance covers the GPU's rounding, which adds in
+    quadrature to the method's error: 2-3e-7 relative in single precision
+    (a few ulps per kernel value, accumulated sum and FFT stage, times the
+    correction factors' amplification) and ~1e-13 in double.
 """
 import math
 
@@ -252,7 +256,15 @@ CASES = [
 
 
 def _exact_bar(eps, e_oracle, prec):
-    return max(2 * eps, e_oracle + (5 * TOL_F32 if prec == 0 else TOL_F64))
+    return max(2 * eps, e_oracle + 0.2 * eps)
+
+
+def _check_exact(name, got, exact, e_oracle, eps, prec):
+    from conftest import record_exact_error
+    e = oracle.rel_l2(got, exact)
+    bar = _exact_bar(eps, e_oracle, prec)
+    record_exact_error(name, eps, e, e_oracle, bar)
+    assert e <= bar, (e, e_oracle, bar)
 
 
 @pytest.mark.parametrize("dim,N,M,eps,prec", CASES)
@@ -271,7 +283,8 @@ def test_type1_parity(nb, dim, N, M, eps, prec, method, iflag):
     assert oracle.rel_l2(f, same_w) < _tol(prec)
     exact = oracle.direct_type1(p64, c.astype(np.complex128), N, iflag)
     e_or = oracle.rel_l2(same_w, exact)
-    assert oracle.rel_l2(f, exact) <= _exact_bar(eps, e_or, prec)
+    _check_exact("type1 %dD N=%s M=%d %s iflag=%+d" % (dim, N, M, method, iflag), f, exact, e_or,
+                 eps, prec)
     p.close()
 
 
@@ -291,7 +304,8 @@ def test_type2_parity(nb, dim, N, M, eps, prec, method, iflag):
     assert oracle.rel_l2(c, same_w) < _tol(prec)
     exact = oracle.direct_type2(p64, f.astype(np.complex128), iflag)
     e_or = oracle.rel_l2(same_w, exact)
-    assert oracle.rel_l2(c, exact) <= _exact_bar(eps, e_or, prec)
+    _check_exact("type2 %dD N=%s M=%d %s iflag=%+d" % (dim, N, M, method, iflag), c, exact, e_or,
+                 eps, prec)
     p.close()
 
 
@@ -460,7 +474,8 @@ def test_sigma125(nb, type_, dim, eps, prec):
     u = 6e-8 if prec == 0 else 1.1e-16
     tol = max(_tol(prec), 4 * u * _amplification(N, eps, 1.25))
     assert oracle.rel_l2(got, same_w) < tol
-    assert oracle.rel_l2(got, exact) <= max(2 * eps, oracle.rel_l2(same_w, exact) + tol)
+    _check_exact("sigma=1.25 type%d %dD N=%s eps=%g" % (type_, dim, N, eps), got, exact,
+                 oracle.rel_l2(same_w, exact), eps, prec)
     p.close()
 
 
