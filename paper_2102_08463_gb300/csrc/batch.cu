@@ -44,7 +44,7 @@ constexpr int kRing = 4;
 struct Group {
     int type = 1, dim = 2, prec = 0, w = 0, method = NUFFT_METHOD_SM;
     int variant = 0;                   // row-sweep form (sweep_variant), part of the key
-    int m1max = 1, tile = 1, smem_optin = 0;
+    int m0max = 1, m1max = 1, tile = 1, smem_optin = 0;
     std::vector<int> members;          // indices into the batch's plans
     size_t smem = 0;                   // max padded-bin bytes over the members
     size_t args_bytes = 0;             // one KArgs<T> per member
@@ -192,6 +192,7 @@ int run_batch(nufft_batch_s *b, void *const *c, void *const *f, bool for_graph)
         ml.smem = g.method == NUFFT_METHOD_SM ? g.smem : 0;
         ml.smem_optin = (size_t)g.smem_optin;
         ml.variant = g.variant;
+        ml.m0max = g.m0max;
         ml.m1max = g.m1max;
         ml.tile = g.tile;
         ml.stream = st;
@@ -260,6 +261,7 @@ int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_
         for (int d = 0; d < p.dim; ++d) cells *= (size_t)padded(p.m[d], p.w);
         g->smem = std::max(g->smem, cells * 2 * real_bytes(p.prec));
         g->tile = std::max(g->tile, (int)cells);
+        g->m0max = std::max(g->m0max, p.m[0]);
         g->m1max = std::max(g->m1max, p.m[1]);
     }
     for (Group &g : b->groups) {

@@ -55,9 +55,15 @@ inline void default_bins(int type, int dim, int prec, int w, int out[3])
         out[1] = 32;
     }
 }
-// Degree of the kernel polynomials: enough for 2e-8 (single) / 1e-14 (double)
-// on the interior window cells at every width.
-__host__ __device__ constexpr int poly_degree(int prec) { return prec == 0 ? 10 : 16; }
+// Degree of the kernel polynomials of width w: the fits of the interior window
+// cells reach eps / 1000 of the smallest tolerance that gives width w (floor
+// 3e-8 single / 1e-14 double): single 6 (w <= 3), 7 (w = 4), 8; double w + 2.
+// Every plan checks its own fit (fit_kernel_poly) and evaluates the kernel
+// directly if the fit misses that bound.
+__host__ __device__ constexpr int poly_degree(int w, int prec)
+{
+    return prec == 0 ? (w <= 3 ? 6 : (w == 4 ? 7 : 8)) : (w + 2 < kPolyTerms - 1 ? w + 2 : kPolyTerms - 1);
+}
 
 // Complex storage types matching cuFFT's interleaved layout.
 template <typename T> struct cplx;
@@ -215,9 +221,7 @@ struct Plan {
     int32_t *vals = nullptr;       // [Mcap]
     int32_t *vals_alt = nullptr;   // [Mcap]
     int32_t *perm = nullptr;       // [Mcap] t: sorted position -> original index
-    void *recs = nullptr;          // [Mcap] rec4<T> per point, execution order (see setpts.cu)
-    void *recs_in = nullptr;       // [Mcap] rec4<T> per point, original order (setpts scratch)
-    int32_t *order = nullptr;      // [Mcap] 3D: execution position -> original index
+    void *recs = nullptr;          // [Mcap] rec4<T> per point, in t order (see setpts.cu)
     void *xyz_copy[3] = {nullptr, nullptr, nullptr};  // coordinate copies for GM
     int32_t *bincount = nullptr;   // [nbins]
     int32_t *binstart = nullptr;   // [nbins]
@@ -324,7 +328,7 @@ struct MultiLaunch {
     size_t smem;               // shared memory per CTA (max over the plans)
     size_t smem_optin;         // largest dynamic shared memory per CTA
     int variant;               // row sweep: 2D lanes (8/16/32), 3D m2 (1/2); 0 = none
-    int m1max;                 // largest bin height over the plans
+    int m0max, m1max;          // largest bin width and height over the plans
     int tile;                  // largest padded bin (cells) over the plans
     cudaStream_t stream;
 };

@@ -160,8 +160,6 @@ void free_points(Plan &p)
     dev_free(p.vals);
     dev_free(p.vals_alt);
     dev_free(p.recs);
-    dev_free(p.recs_in);
-    dev_free(p.order);
     dev_free(p.subprob);
     for (int d = 0; d < 3; ++d) {
         dev_free(p.xyz_copy[d]);
@@ -169,8 +167,6 @@ void free_points(Plan &p)
     }
     p.keys = p.keys_alt = p.vals = p.vals_alt = p.perm = nullptr;
     p.recs = nullptr;
-    p.recs_in = nullptr;
-    p.order = nullptr;
     p.subprob = nullptr;
     p.Mcap = 0;
     p.maxsub = 0;
@@ -239,7 +235,7 @@ static double kernel_cell_value(int w, double beta, int i, double s)
 
 void nufft::fit_kernel_poly(Plan &p)
 {
-    const int w = p.w, D = poly_degree(p.prec);
+    const int w = p.w, D = poly_degree(p.w, p.prec);
     const double PI = 3.14159265358979323846;
     for (int i = 0; i < kMaxW; ++i)
         for (int d = 0; d < kPolyTerms; ++d) p.poly[i][d] = 0.0;
@@ -281,7 +277,7 @@ void nufft::fit_kernel_poly(Plan &p)
             if (e > worst) worst = e;
         }
     }
-    p.poly_ok = worst <= (p.prec == 0 ? 3e-8 : 1e-14);
+    p.poly_ok = worst <= fmax(p.eps * 1e-3, p.prec == 0 ? 3e-8 : 1e-14);
 }
 
 int nufft::sweep_variant(const Plan &p)
@@ -588,8 +584,6 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
         if (rc == NUFFT_OK) rc = dev_alloc(&p.vals, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.vals_alt, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.recs, rsz * cap);
-        if (rc == NUFFT_OK) rc = dev_alloc(&p.recs_in, rsz * cap);
-        if (rc == NUFFT_OK && p.dim == 3) rc = dev_alloc(&p.order, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.subprob, sizeof(int4) * maxsub);
         if (rc != NUFFT_OK) {
             free_points(p);

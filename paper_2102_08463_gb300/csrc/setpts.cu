@@ -14,11 +14,9 @@
 //     order (or, on request, in shared-atomic order).
 //   LSD radix sort (many bins): 8-bit digits, per-CTA digit histograms, a scan
 //     of the digit x CTA matrix, ranked scatter; every pass is stable.
-// The ranked scatter also stores each point's packed record in its sorted slot
-// (computed from the coordinates it reads in order); a last pass
-// (exec_order_kernel) orders the points of every subproblem by the first row,
-// plane and column of their window and copies their records in that order,
-// which is the order the spreading and interpolation kernels read them in.
+// A last pass writes every point's packed record in t order (coordinates
+// gathered through t), so that the spreading and interpolation kernels read
+// the records of a subproblem as one contiguous run.
 #include "nufft_internal.cuh"
 
 namespace nufft {
@@ -370,16 +368,11 @@ bin_offsets_kernel(const int32_t *__restrict__ bincount, const int2 *__restrict_
 //     turns; a CTA's points of one bin fill its run of slots in atomic order.
 constexpr int kRankU = 4;
 
-// kRecs: also write each point's packed record into its sorted slot (record of
-// the point's own bin; in 2D the z slot carries the point's index), computed
-// from its coordinates -- a scattered store instead of a later gather.
-template <bool kOrdered, typename T, int DIM, bool kRecs>
+template <bool kOrdered>
 __global__ void __launch_bounds__(kCountThreads)
 rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restrict__ keys,
                     const int32_t *__restrict__ mat, const int32_t *__restrict__ binstart,
-                    int32_t *__restrict__ perm, const T *__restrict__ x, const T *__restrict__ y,
-                    const T *__restrict__ z, int3 n, int3 m, int w,
-                    typename rec4<T>::type *__restrict__ recs)
+                    int32_t *__restrict__ perm)
 {
     extern __shared__ int run[];   // next output slot per bin for this CTA
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -394,28 +387,17 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
     const int64_t tile = (int64_t)nwarps * 32 * kRankU;
     const int64_t mine0 = (int64_t)warp * 32 * kRankU + lane;
     int key[kRankU], keyn[kRankU];
-    T xv[kRankU], yv[kRankU], zv[kRankU];
 #pragma unroll
     for (int u = 0; u < kRankU; ++u) {
         const int64_t j = beg + mine0 + u * 32;
         key[u] = j < end ? keys[j] : -1;
     }
     for (int64_t t0 = beg; t0 < end; t0 += tile) {
-        if (kRecs) {
-#pragma unroll
-            for (int u = 0; u < kRankU; ++u) {
-                const int64_t j = t0 + mine0 + u * 32;
-                xv[u] = j < end ? x[j] : (T)0;
-                yv[u] = j < end ? y[j] : (T)0;
-                zv[u] = (DIM == 3 && j < end) ? z[j] : (T)0;
-            }
-        }
 #pragma unroll
         for (int u = 0; u < kRankU; ++u) {
             const int64_t j = t0 + tile + mine0 + u * 32;
             keyn[u] = j < end ? keys[j] : -1;
         }
-        int slot[kRankU];
         if (kOrdered) {
             unsigned peers[kRankU];
             int base[kRankU];
@@ -436,38 +418,32 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
                 __syncthreads();
             }
 #pragma unroll
-            for (int u = 0; u < kRankU; ++u)
-                slot[u] = __shfl_sync(kFull, base[u], __ffs(peers[u]) - 1) +
-                          __popc(peers[u] & lt_mask);
+            for (int u = 0; u < kRankU; ++u) {
+                const int b = __shfl_sync(kFull, base[u], __ffs(peers[u]) - 1);
+                if (key[u] >= 0)
+                    perm[b + __popc(peers[u] & lt_mask)] = (int32_t)(t0 + mine0 + u * 32);
+            }
         } else {
+            int slot[kRankU];
 #pragma unroll
             for (int u = 0; u < kRankU; ++u)
                 slot[u] = key[u] >= 0 ? atomicAdd(&run[key[u]], 1) : 0;
-        }
 #pragma unroll
-        for (int u = 0; u < kRankU; ++u) {
-            if (key[u] >= 0) {
-                const int32_t j = (int32_t)(t0 + mine0 + u * 32);
-                perm[slot[u]] = j;
-                if (kRecs) {
-                    typename rec4<T>::type r = make_record_v<T, DIM>(xv[u], yv[u], zv[u], n, m, w);
-                    if (DIM == 2) r.z = packed_word<T>((uint32_t)j);
-                    recs[slot[u]] = r;
-                }
-            }
+            for (int u = 0; u < kRankU; ++u)
+                if (key[u] >= 0) perm[slot[u]] = (int32_t)(t0 + mine0 + u * 32);
         }
 #pragma unroll
         for (int u = 0; u < kRankU; ++u) key[u] = keyn[u];
     }
 }
 
-// Records in t order for the radix path: recs[i] = record of point perm[i]
-// (gathered coordinates).
+// Packed records in t order: recs[i] = record of point perm[i] (gathered
+// coordinates); in 2D the z slot carries the point's index.
 template <typename T, int DIM>
-__global__ void records_from_perm_kernel(const int32_t *__restrict__ perm, int64_t M,
-                                         const T *__restrict__ x, const T *__restrict__ y,
-                                         const T *__restrict__ z, int3 n, int3 m, int w,
-                                         typename rec4<T>::type *__restrict__ recs)
+__global__ void __launch_bounds__(256)
+records_from_perm_kernel(const int32_t *__restrict__ perm, int64_t M, const T *__restrict__ x,
+                         const T *__restrict__ y, const T *__restrict__ z, int3 n, int3 m, int w,
+                         typename rec4<T>::type *__restrict__ recs)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -596,146 +572,6 @@ __global__ void write_subs_kernel(const int32_t *__restrict__ bincount,
     }
 }
 
-// ---------------------------------------------------------------------------
-// Execution order (after the sort): inside every subproblem the points are
-// ordered by the first row of their window, then (3D) its first plane, then its
-// first column, ties in t order, and their records are copied in that order, so
-// the spreading and interpolation kernels read records as contiguous runs with
-// the rows of a subproblem non-decreasing.  3D plans also get order[] = the
-// original index at each position (2D records carry it in their z slot).  The
-// input is the records in t order (written by the ranked scatter), so every
-// read stays inside the subproblem's contiguous run.  One warp per subproblem,
-// in pieces of at most kOrderCap points, each piece ordered on its own: the
-// window starts go to shared memory, one stable counting sort by the combined
-// key, then the records are copied.
-// ---------------------------------------------------------------------------
-constexpr int kOrderCap = 2048;
-constexpr int kOrderWarps = 4;
-constexpr int kOrderMaxKeys = 4096;
-
-// Stable counting sort of items 0 .. n-1 (one warp) by key_of(i) in [0, nk);
-// dst[] receives the items grouped by key, in index order inside a key.
-// cnt[] holds nk + 1 ints.
-template <typename KeyOf>
-__device__ __forceinline__ void warp_counting_sort(int n, int nk, uint16_t *dst, int *cnt,
-                                                   KeyOf key_of)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int i = lane; i <= nk; i += 32) cnt[i] = 0;
-    __syncwarp();
-    for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        const int key = i < n ? key_of(i) : 0x7fffffff;
-        const unsigned peers = __match_any_sync(kFull, key);
-        if (i < n && (peers & lt) == 0) atomicAdd(&cnt[key + 1], __popc(peers));
-    }
-    __syncwarp();
-    int running = 0;
-    for (int i0 = 0; i0 <= nk; i0 += 32) {
-        const int i = i0 + lane;
-        int v = i <= nk ? cnt[i] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, v, o);
-            if (lane >= o) v += t;
-        }
-        if (i <= nk) cnt[i] = running + v;
-        running += __shfl_sync(kFull, v, 31);
-    }
-    __syncwarp();
-    for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        const int key = i < n ? key_of(i) : 0x7fffffff;
-        const unsigned peers = __match_any_sync(kFull, key);
-        const int leader = __ffs(peers) - 1;
-        int pos = 0;
-        if (i < n && lane == leader) pos = atomicAdd(&cnt[key], __popc(peers));
-        pos = __shfl_sync(kFull, pos, leader);
-        if (i < n) dst[pos + __popc(peers & lt)] = (uint16_t)i;
-    }
-    __syncwarp();
-}
-
-// Shared memory of one warp: the window starts (u32) and the sorted positions
-// (u16) of kOrderCap points, then nk + 1 counters.
-__host__ __device__ inline size_t order_warp_bytes(int nk)
-{
-    return (size_t)kOrderCap * 6 + (size_t)4 * (nk + 1);
-}
-
-// Sort key of a packed window start: (row, plane, column) with kx columns and
-// kz planes; kz = 0 drops the plane, kx = 0 drops the column.
-__device__ __forceinline__ int order_key(uint32_t pk, int kx, int kz)
-{
-    int k = (int)((pk >> 10) & 1023u);
-    if (kz > 0) k = k * kz + (int)(pk >> 20);
-    if (kx > 0) k = k * kx + (int)(pk & 1023u);
-    return k;
-}
-
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kOrderWarps * 32)
-exec_order_kernel(const int32_t *__restrict__ perm, const int4 *__restrict__ subprob,
-                  const int32_t *__restrict__ nsub, int nk, int kx, int kz,
-                  const typename rec4<T>::type *__restrict__ recs_t,
-                  typename rec4<T>::type *__restrict__ recs, int32_t *__restrict__ order)
-{
-    using R = typename rec4<T>::type;
-    constexpr int U = 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char *sm = smem_raw + (size_t)warp * order_warp_bytes(nk);
-    uint32_t *spk = reinterpret_cast<uint32_t *>(sm);
-    uint16_t *idx = reinterpret_cast<uint16_t *>(sm + (size_t)kOrderCap * 4);
-    int *cnt = reinterpret_cast<int *>(sm + (size_t)kOrderCap * 6);
-    const int ns = *nsub;
-    for (int sp = blockIdx.x * kOrderWarps + warp; sp < ns; sp += gridDim.x * kOrderWarps) {
-        const int4 sub = subprob[sp];
-        for (int piece = 0; piece < sub.z; piece += kOrderCap) {
-            const int np = min(kOrderCap, sub.z - piece);
-            const int s0 = sub.y + piece;
-            for (int k0 = 0; k0 < np; k0 += 32 * U) {
-                uint32_t pk[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int k = k0 + u * 32 + lane;
-                    pk[u] = k < np ? unpack_word_t<T>(recs_t[s0 + k].w) : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int k = k0 + u * 32 + lane;
-                    if (k < np) spk[k] = pk[u];
-                }
-            }
-            __syncwarp();
-            warp_counting_sort(np, nk, idx, cnt, [&](int i) { return order_key(spk[i], kx, kz); });
-            for (int k0 = 0; k0 < np; k0 += 32 * U) {
-                R rc[U];
-                int j[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int k = k0 + u * 32 + lane;
-                    if (k < np) {
-                        const int src = s0 + idx[k];
-                        rc[u] = recs_t[src];
-                        if (DIM == 3) j[u] = perm[src];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int k = k0 + u * 32 + lane;
-                    if (k < np) {
-                        recs[s0 + k] = rc[u];
-                        if (DIM == 3) order[s0 + k] = j[u];
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
 inline int grid_for(int64_t work, int threads, int num_sms)
 {
     int64_t b = (work + threads - 1) / threads;
@@ -841,46 +677,27 @@ int radix_sort_blocks(const Plan &p, int64_t M)
 
 namespace {
 
-// Key space of the execution order: (row, plane, column) when it fits the
-// counters, else (row, plane), else rows alone.
-void exec_order_keys(const Plan &p, int *nk, int *kx, int *kz)
-{
-    const int64_t rows = p.m[1] + 1, pl = p.dim == 3 ? p.m[2] + 1 : 1, cols = p.m[0] + 1;
-    *kz = p.dim == 3 ? (int)pl : 0;
-    *kx = (int)cols;
-    if (rows * pl * cols <= kOrderMaxKeys) {
-        *nk = (int)(rows * pl * cols);
-        return;
-    }
-    *kx = 0;
-    if (rows * pl <= kOrderMaxKeys) {
-        *nk = (int)(rows * pl);
-        return;
-    }
-    *kz = 0;
-    *nk = (int)rows;
-}
-
+// Packed records in t order: recs[i] = record of point t[i] (coordinates
+// gathered through t: they were read moments before by the counting pass and
+// sit in L2), written in order so that the spreading and interpolation kernels
+// read every subproblem's records as one contiguous run.
 template <typename T>
-cudaError_t launch_exec_order(Plan &p, const typename rec4<T>::type *recs_t)
+cudaError_t launch_records(Plan &p, const T *x, const T *y, const T *z,
+                           typename rec4<T>::type *recs)
 {
-    int nk = 0, kx = 0, kz = 0;
-    exec_order_keys(p, &nk, &kx, &kz);
-    const size_t smem = order_warp_bytes(nk) * kOrderWarps;
-    auto k = p.dim == 2 ? exec_order_kernel<T, 2> : exec_order_kernel<T, 3>;
-    cudaError_t e = allow_max_smem((const void *)k);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kOrderWarps * 32, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t want = (p.maxsub + kOrderWarps - 1) / kOrderWarps;
-    int64_t grid = (int64_t)p.num_sms * (per_sm < 1 ? 1 : per_sm);
-    if (grid > want) grid = want;
-    if (grid < 1) grid = 1;
+    const int3 n = make_int3((int)p.nf[0], (int)p.nf[1], (int)p.nf[2]);
+    const int3 m = make_int3(p.m[0], p.m[1], p.m[2]);
+    int64_t g = (p.M + 255) / 256;
+    const int64_t cap = (int64_t)p.num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
     count_launch();
-    k<<<(unsigned)grid, kOrderWarps * 32, smem, p.stream>>>(
-        p.perm, p.subprob, p.nsub, nk, kx, kz, recs_t,
-        reinterpret_cast<typename rec4<T>::type *>(p.recs), p.order);
+    if (p.dim == 2)
+        records_from_perm_kernel<T, 2><<<(unsigned)g, 256, 0, p.stream>>>(p.perm, p.M, x, y, z, n,
+                                                                         m, p.w, recs);
+    else
+        records_from_perm_kernel<T, 3><<<(unsigned)g, 256, 0, p.stream>>>(p.perm, p.M, x, y, z, n,
+                                                                         m, p.w, recs);
     return cudaGetLastError();
 }
 
@@ -893,7 +710,7 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
     const int3 m = make_int3(p.m[0], p.m[1], p.m[2]);
     const int3 nb = make_int3(p.nb[0], p.nb[1], p.nb[2]);
     const int nbins = (int)p.nbins;
-    auto *recs = reinterpret_cast<typename rec4<T>::type *>(p.recs_in);
+    auto *recs = reinterpret_cast<typename rec4<T>::type *>(p.recs);
     cudaError_t e = cudaSuccess;
     if (M == 0) {
         e = cudaMemsetAsync(p.bincount, 0, sizeof(int32_t) * p.nbins, st);
@@ -905,10 +722,7 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
         const int64_t chunk = (M + cblk - 1) / cblk;
         const size_t smem = (size_t)nbins * sizeof(int32_t);
         auto kc = p.dim == 2 ? count_kernel<T, 2> : count_kernel<T, 3>;
-        auto ks = p.dim == 2 ? (p.unordered_bins ? rank_scatter_kernel<false, T, 2, true>
-                                                 : rank_scatter_kernel<true, T, 2, true>)
-                             : (p.unordered_bins ? rank_scatter_kernel<false, T, 3, true>
-                                                 : rank_scatter_kernel<true, T, 3, true>);
+        auto ks = p.unordered_bins ? rank_scatter_kernel<false> : rank_scatter_kernel<true>;
         e = allow_max_smem((const void *)kc);
         if (e == cudaSuccess) e = allow_max_smem((const void *)ks);
         if (e != cudaSuccess) return e;
@@ -919,12 +733,11 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
                                                                          p.bincount, p.msub, agg);
         bin_offsets_kernel<<<(nbins + kOffThreads - 1) / kOffThreads, kOffThreads, 0, st>>>(
             p.bincount, agg, nbins, p.msub, p.binstart, p.subprob, p.nsub);
-        ks<<<cblk, kCountThreads, smem, st>>>(M, chunk, nbins, p.keys, p.mat, p.binstart, p.vals,
-                                              x, y, z, n, m, p.w, recs);
+        ks<<<cblk, kCountThreads, smem, st>>>(M, chunk, nbins, p.keys, p.mat, p.binstart, p.vals);
         p.perm = p.vals;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return launch_exec_order<T>(p, recs);
+        return launch_records<T>(p, x, y, z, recs);
     } else {
         const int g = grid_for(M, 256, p.num_sms);
         count_launch();
@@ -970,19 +783,12 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
     }
     e = launch_scan(p, p.scan_tmp, p.scan_tmp, nbins, p.nsub);
     if (e != cudaSuccess) return e;
-    count_launch(2);
+    count_launch();
     write_subs_kernel<<<grid_for(nbins, 256, p.num_sms), 256, 0, st>>>(
         p.bincount, p.binstart, p.scan_tmp, nbins, p.msub, p.subprob);
-    {
-        const int g = grid_for(M, 256, p.num_sms);
-        if (p.dim == 2)
-            records_from_perm_kernel<T, 2><<<g, 256, 0, st>>>(p.perm, M, x, y, z, n, m, p.w, recs);
-        else
-            records_from_perm_kernel<T, 3><<<g, 256, 0, st>>>(p.perm, M, x, y, z, n, m, p.w, recs);
-    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_exec_order<T>(p, recs);
+    return launch_records<T>(p, x, y, z, recs);
 }
 
 }  // namespace
@@ -1035,7 +841,7 @@ cudaError_t binsort_into_impl(const BinsortScratch &s, int dim, int64_t M, const
     auto kc = dim == 2 ? count_keys_kernel<T, 2> : count_keys_kernel<T, 3>;
     cudaError_t e = allow_max_smem((const void *)kc);
     if (e != cudaSuccess) return e;
-    e = allow_max_smem((const void *)rank_scatter_kernel<true, float, 2, false>);
+    e = allow_max_smem((const void *)rank_scatter_kernel<true>);
     if (e != cudaSuccess) return e;
     count_launch(3);
     kc<<<s.nblk, kCountThreads, smem, st>>>(x, y, z, M, chunk, n, m, nb, nbins, s.keys, s.mat);
@@ -1046,9 +852,8 @@ cudaError_t binsort_into_impl(const BinsortScratch &s, int dim, int64_t M, const
     scan_plan.scan_part = s.scan_part;
     e = launch_scan(scan_plan, bincount, s.binstart, nbins, nullptr);
     if (e != cudaSuccess) return e;
-    rank_scatter_kernel<true, float, 2, false><<<s.nblk, kCountThreads, smem, st>>>(
-        M, chunk, nbins, s.keys, s.mat, s.binstart, perm, nullptr, nullptr, nullptr, n, m, 0,
-        nullptr);
+    rank_scatter_kernel<true><<<s.nblk, kCountThreads, smem, st>>>(M, chunk, nbins, s.keys, s.mat,
+                                                                   s.binstart, perm);
     return cudaGetLastError();
 }
 

@@ -28,8 +28,8 @@ constexpr unsigned kFullMask = 0xffffffffu;
 
 template <typename T>
 struct alignas(16) KArgs {
-    const typename rec4<T>::type *recs;          // packed records, execution order
-    const int32_t *order;                        // 3D: execution position -> point index
+    const typename rec4<T>::type *recs;          // packed records, in t order
+    const int32_t *order;                        // t: sorted position -> point index
     const int4 *subprob;
     const int32_t *nsub;
     const T *xyz0, *xyz1, *xyz2;                 // coordinates (GM kernels)
@@ -65,31 +65,12 @@ __device__ __forceinline__ int point_of(const KArgs<T> &a, const typename rec4<T
     return DIM == 2 ? (int)unpack_word<T>(r.z) : a.order[pos];
 }
 
-// Packed single-precision pairs: two floats in one 64-bit register pair, for
-// the f32x2 arithmetic of sm_100-class GPUs (one instruction for both lanes).
-__device__ __forceinline__ uint64_t pack2(float lo, float hi)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float2 unpack2(uint64_t v)
-{
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-}
-// acc += a * b, lane by lane
-__device__ __forceinline__ void fma2(uint64_t &acc, uint64_t a, uint64_t b)
-{
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
+// Packed single-precision pairs: the f32x2 arithmetic of sm_100-class GPUs
+// (one instruction for both halves of a float2), through the compiler's
+// builtins so that it allocates the register pairs itself.
+// acc += a * b, half by half
+__device__ __forceinline__ void fma2(float2 &acc, float2 a, float2 b) { acc = __ffma2_rn(a, b, acc); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 __device__ __forceinline__ int wrap_any(int v, int n)
 {
@@ -276,24 +257,24 @@ spread_sm_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restr
 // padded bin (p0 = m0 + W <= L) and holds, in registers, the W rows that a
 // window starting at the current row can reach.
 //
-//  1. setpts left the subproblem's records ordered by the first row of their
-//     window (then column; see setpts.cu), so the warp reads them as one
-//     contiguous run, 32 at a time, with the strengths c gathered by index.
+//  1. The subproblem's records (one contiguous run in t order) are ordered by
+//     the first row of their window: a stable counting sort in shared memory
+//     (warp-aggregated integer atomics), whose counters then mark where each
+//     start row's points end; the records are read in that order, 32 at a
+//     time, with the strengths c gathered by index.
 //  2. Lane i evaluates point i's 2W kernel values and stores w_y and c w_x in a
-//     staging slot.
-//  3. The warp walks the staged points one start row at a time.  Before row r
-//     is entered, every row above r is complete: the sub-warps' copies of it are
-//     summed by shuffles, added to the fine grid (periodic wrap), and the
-//     register window shifts down one row.  The points starting at row r are
-//     dealt to the sub-warps in turn; every lane adds (c w_x[q - s_x]) w_y[k] to
-//     its W rows -- a plain register update, since within a sub-warp no two
-//     lanes own the same cell.  In single precision each row is one packed
-//     (re, im) register pair updated by one f32x2 FMA.  A start row lower than
-//     the current one (a new ordering piece of a long subproblem) flushes the
-//     whole window first.
-//  4. The rows still held at the end are added to the fine grid.
+//     staging slot.  The W window rows live in register slots indexed by row
+//     mod W; w_y is stored rotated the same way.
+//  3. The warp walks the padded rows in blocks of W (row rb + k in slot k, a
+//     compile-time index): the points starting at the row are dealt to the
+//     sub-warps -- every lane adds (c w_x[q - s_x]) w_y to its W slots, a plain
+//     register update, since within a sub-warp no two lanes own the same cell;
+//     in single precision one f32x2 FMA per slot -- and then the row is
+//     complete: the sub-warps' copies are summed by shuffles, added to the
+//     fine grid (periodic wrap) and the slot cleared.
 //
-// Shared memory per warp (sweep_bytes): 32 staging slots.
+// Shared memory per warp (sweep_bytes): the sorted positions, the row counters
+// and 32 staging slots.
 // ---------------------------------------------------------------------------
 // Staging slots are built from 16-byte quads (4 floats or 2 doubles), with an
 // odd quad count so that the 8 lanes of a quarter-warp storing their slots with
@@ -367,10 +348,77 @@ __device__ __forceinline__ void store_dup_row(float *dst, const float (&v)[W])
     }
 }
 
-template <typename T, int W, int L>
-__host__ __device__ inline size_t sweep_bytes()
+// The row sweeps order a subproblem's points by window start row themselves,
+// in pieces of at most kSweepCap points (each piece swept on its own): warp
+// shared memory holds the piece's sorted positions (u16), the key counters and
+// the 32 staging slots.
+constexpr int kSweepCap = 1024;
+
+__host__ __device__ inline size_t sweep_head(int nkeys)
 {
-    return sizeof(T) * (size_t)32 * sweep2_slot<T, W, L>();
+    return ((size_t)2 * kSweepCap + (size_t)4 * (nkeys + 1) + 15) & ~(size_t)15;
+}
+
+template <typename T, int W, int L>
+__host__ __device__ inline size_t sweep_bytes(int m1)
+{
+    return sweep_head(m1 + 1) + sizeof(T) * (size_t)32 * sweep2_slot<T, W, L>();
+}
+
+// Stable counting sort (one warp) of the n records of a piece by key_of(record
+// packed word) in [0, nkeys): idx[] receives the positions grouped by key,
+// increasing inside a key; afterwards cnt[k] is the end of key k's run.  cnt[]
+// holds nkeys + 1 ints.  The packed words are read from the records (coalesced).
+template <typename T, typename KeyOf>
+__device__ __forceinline__ void warp_sort_records(const typename rec4<T>::type *recs, int n,
+                                                  int nkeys, uint16_t *idx, int *cnt, KeyOf key_of)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = lane; i <= nkeys; i += 32) cnt[i] = 0;
+    __syncwarp();
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const int key = i < n ? key_of(unpack_word<T>(recs[i].w)) : 0x7fffffff;
+        const unsigned peers = __match_any_sync(kFullMask, key);
+        if (i < n && (peers & lt) == 0) atomicAdd(&cnt[key + 1], __popc(peers));
+    }
+    __syncwarp();
+    int running = 0;
+    for (int i0 = 0; i0 <= nkeys; i0 += 32) {
+        const int i = i0 + lane;
+        int v = i <= nkeys ? cnt[i] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFullMask, v, o);
+            if (lane >= o) v += t;
+        }
+        if (i <= nkeys) cnt[i] = running + v;
+        running += __shfl_sync(kFullMask, v, 31);
+    }
+    __syncwarp();
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const int key = i < n ? key_of(unpack_word<T>(recs[i].w)) : 0x7fffffff;
+        const unsigned peers = __match_any_sync(kFullMask, key);
+        const int leader = __ffs(peers) - 1;
+        int pos = 0;
+        if (i < n && lane == leader) pos = atomicAdd(&cnt[key], __popc(peers));
+        pos = __shfl_sync(kFullMask, pos, leader);
+        if (i < n) idx[pos + __popc(peers & lt)] = (uint16_t)i;
+    }
+    __syncwarp();
+}
+
+// By window start row (ZMUL = 0) or row * ZMUL + start plane (3D).
+template <typename T, int ZMUL>
+__device__ __forceinline__ void sweep_row_order(const typename rec4<T>::type *recs, int n,
+                                                int nkeys, uint16_t *idx, int *cnt)
+{
+    warp_sort_records<T>(recs, n, nkeys, idx, cnt, [](uint32_t pk) {
+        const int row = (int)((pk >> 10) & 1023u);
+        return ZMUL == 0 ? row : row * ZMUL + (int)(pk >> 20);
+    });
 }
 
 // Single-precision ES kernel for the staging step, written without the
@@ -397,7 +445,7 @@ __device__ __forceinline__ double es_kernel_stage(double z, double beta)
 template <typename T, int W>
 __device__ __forceinline__ void kernel_row(const KArgs<T> &a, T delta, T (&v)[W])
 {
-    constexpr int D = poly_degree(sizeof(T) == 4 ? 0 : 1);
+    constexpr int D = poly_degree(W, sizeof(T) == 4 ? 0 : 1);
     if (a.poly) {
         const T s = (T)2 * (delta - (T)(0.5 * W - 1)) - (T)1;
 #pragma unroll
@@ -419,7 +467,7 @@ __device__ __forceinline__ void kernel_row(const KArgs<T> &a, T delta, T (&v)[W]
 template <typename T, int W>
 __device__ __forceinline__ T kernel_cell(const KArgs<T> &a, T delta, int i)
 {
-    constexpr int D = poly_degree(sizeof(T) == 4 ? 0 : 1);
+    constexpr int D = poly_degree(W, sizeof(T) == 4 ? 0 : 1);
     if (a.poly && i > 0 && i < W - 1) {
         const T s = (T)2 * (delta - (T)(0.5 * W - 1)) - (T)1;
         T acc = a.coef[i][D];
@@ -456,7 +504,8 @@ __device__ __forceinline__ void load_row(const double *s, double (&v)[W])
 }
 
 template <typename T, int W, int L>
-__device__ __forceinline__ void spread_sweep2_sub(const KArgs<T> &a, int4 sub, int tr, T *stg)
+__device__ __forceinline__ void spread_sweep2_sub(const KArgs<T> &a, int4 sub, int tr,
+                                                  unsigned char *sm)
 {
     using C = typename cplx<T>::type;
     using R = typename rec4<T>::type;
@@ -466,6 +515,9 @@ __device__ __forceinline__ void spread_sweep2_sub(const KArgs<T> &a, int4 sub, i
     constexpr int OCX = sweep2_wy_quads<T, W>() * quad_vec<T>();
     const int lane = threadIdx.x & 31, h = lane / L, q = lane % L;
     const int n = sub.z;
+    uint16_t *idx = reinterpret_cast<uint16_t *>(sm);
+    int *cnt = reinterpret_cast<int *>(sm + 2 * kSweepCap);
+    T *stg = reinterpret_cast<T *>(sm + sweep_head(a.m1 + 1));
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
     const int P = pad_lo(W);
@@ -473,151 +525,162 @@ __device__ __forceinline__ void spread_sweep2_sub(const KArgs<T> &a, int4 sub, i
     C *grid = a.grid + (int64_t)tr * a.nftot;
     const bool writer = h == 0 && q < a.p0;
     const int gx = wrap_any(o0 - P + (q < a.p0 ? q : 0), a.n0);
-    const int row0 = o1 - P;
-    // window row k: accp[k] = (re, im) packed (single), accr[k] / acci[k] (double)
-    uint64_t accp[F32 ? W : 1];
+    const int grow0 = wrap_any(o1 - P, a.n1);            // fine-grid row of padded row 0
+    // Window slot s holds the padded row r with r mod W = s: (re, im) as a float2
+    // (single) or accr / acci (double).  A staged point's w_y is stored rotated
+    // the same way, so every update touches the slots in a fixed order.
+    float2 accp[F32 ? W : 1];
     T accr[F32 ? 1 : W], acci[F32 ? 1 : W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        if constexpr (F32) accp[k] = 0ull;
+        if constexpr (F32) accp[k] = make_float2(0.f, 0.f);
         else accr[k] = acci[k] = (T)0;
     }
-    int row = 0;                                          // padded row held in row slot 0
-
-    auto flush_row = [&](int r_rel, T vr, T vi) {
+    // add slot k to fine-grid row g (sub-warp copies summed by shuffles) and clear it
+    auto flush = [&](int k, int g) {
+        T vr, vi;
+        if constexpr (F32) {
+            vr = accp[k < W ? k : 0].x;
+            vi = accp[k < W ? k : 0].y;
+            accp[k < W ? k : 0] = make_float2(0.f, 0.f);
+        } else {
+            vr = accr[k < W ? k : 0];
+            vi = acci[k < W ? k : 0];
+            accr[k < W ? k : 0] = acci[k < W ? k : 0] = (T)0;
+        }
 #pragma unroll
         for (int o = L; o < 32; o <<= 1) {
             vr += __shfl_xor_sync(kFullMask, vr, o);
             vi += __shfl_xor_sync(kFullMask, vi, o);
         }
         if (writer && (vr != (T)0 || vi != (T)0))
-            atomic_add_cplx(&grid[(int64_t)wrap_any(row0 + r_rel, a.n1) * a.n0 + gx], vr, vi);
+            atomic_add_cplx(&grid[(int64_t)g * a.n0 + gx], vr, vi);
     };
-    auto flush_slot = [&](int k, int r_rel) {
+    // one staged point: lane q adds (c w_x)[q] w_y to the W window rows
+    auto step = [&](int i) {
+        const T *s = stg + i * SLOT;
         if constexpr (F32) {
-            const float2 v = unpack2(accp[k < W ? k : 0]);
-            flush_row(r_rel, v.x, v.y);
+            const float2 cx = *reinterpret_cast<const float2 *>(s + OCX + 2 * q);
+#pragma unroll
+            for (int k = 0; k < W; k += 2) {
+                const float4 wp = *reinterpret_cast<const float4 *>(s + 2 * k);
+                fma2(accp[k], cx, make_float2(wp.x, wp.y));
+                if (k + 1 < W) fma2(accp[k + 1 < W ? k + 1 : k], cx, make_float2(wp.z, wp.w));
+            }
         } else {
-            flush_row(r_rel, accr[k < W ? k : 0], acci[k < W ? k : 0]);
+            const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * q);
+            T wy[W];
+            load_row<W>(s, wy);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                accr[k] += cx.x * wy[k];
+                acci[k] += cx.y * wy[k];
+            }
         }
     };
 
-    R rc;
-    C cv;
-    auto fetch = [&](int base) {
-        if (base + lane < n) {
-            rc = a.recs[sub.y + base + lane];
+    const R *recs = a.recs + sub.y;
+    for (int piece = 0; piece < n; piece += kSweepCap) {
+        const int np = min(kSweepCap, n - piece);
+        // points by window start row; afterwards cnt[r] = end of start row r
+        sweep_row_order<T, 0>(recs + piece, np, a.m1 + 1, idx, cnt);
+        R rc;
+        C cv;
+        if (lane < np) {
+            rc = recs[piece + idx[lane]];
             cv = cin[unpack_word<T>(rc.z)];
         }
-    };
-    fetch(0);
-    for (int base = 0; base < n; base += 32) {
-        const int cnt = min(32, n - base);
-        int myrow = 0x7fffffff;
-        if (lane < cnt) {
-            const uint32_t pk = unpack_word<T>(rc.w);
-            T *s = stg + lane * SLOT;
-            myrow = (int)((pk >> 10) & 1023u);
-            const int sx = (int)(pk & 1023u);
-            T vx[W], vy[W];
-            kernel_row<T, W>(a, rc.x, vx);
-            kernel_row<T, W>(a, rc.y, vy);
+        int bbase = -32, bend = 0;                         // staged positions [bbase, bend)
+        auto stage_next = [&]() {
+            __syncwarp();                                  // the old slots are consumed
+            bbase += 32;
+            const int c = min(32, np - bbase);
+            if (lane < c) {
+                const uint32_t pk = unpack_word<T>(rc.w);
+                T *s = stg + lane * SLOT;
+                const int sy = (int)((pk >> 10) & 1023u);
+                const int sx = (int)(pk & 1023u);
+                T vx[W], vy[W];
+                kernel_row<T, W>(a, rc.x, vx);
+                kernel_row<T, W>(a, rc.y, vy);
 #pragma unroll
-            for (int k = 0; k < 2 * L; k += quad_vec<T>()) store_zero_quad(s + OCX + k);
+                for (int k = 0; k < 2 * L; k += quad_vec<T>()) store_zero_quad(s + OCX + k);
 #pragma unroll
-            for (int i = 0; i < W; ++i) {
-                C v;
-                v.x = cv.x * vx[i];
-                v.y = cv.y * vx[i];
-                *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) = v;
-            }
-            if constexpr (F32) store_dup_row<W>(s, vy);
-            else store_row<W>(s, vy);
-        }
-        if (base == 0) row = __shfl_sync(kFullMask, myrow, 0);
-        fetch(base + 32);
-        __syncwarp();
-        int i0 = 0;
-        while (i0 < cnt) {
-            const int r = __shfl_sync(kFullMask, myrow, i0);
-            if (r != row) {
-                if (r > row && r < row + W) {
-                    do {                                  // rows above r are complete
-                        flush_slot(0, row);
+                for (int i = 0; i < W; ++i) {
+                    C v;
+                    v.x = cv.x * vx[i];
+                    v.y = cv.y * vx[i];
+                    *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) = v;
+                }
+                int slot = sy % W;                         // w_y[k] goes to slot (sy + k) mod W
 #pragma unroll
-                        for (int k = 0; k + 1 < W; ++k) {
-                            if constexpr (F32) accp[k] = accp[k + 1];
-                            else {
-                                accr[k] = accr[k + 1];
-                                acci[k] = acci[k + 1];
-                            }
-                        }
-                        if constexpr (F32) accp[W - 1] = 0ull;
-                        else accr[W - 1] = acci[W - 1] = (T)0;
-                        ++row;
-                    } while (row < r);
-                } else {                                  // jump: the whole window is complete
-#pragma unroll
-                    for (int k = 0; k < W; ++k) {
-                        flush_slot(k, row + k);
-                        if constexpr (F32) accp[k] = 0ull;
-                        else accr[k] = acci[k] = (T)0;
-                    }
-                    row = r;
+                for (int k = 0; k < W; ++k) {
+                    if constexpr (F32)
+                        *reinterpret_cast<float2 *>(s + 2 * slot) = make_float2(vy[k], vy[k]);
+                    else
+                        s[slot] = vy[k];
+                    slot = slot + 1 == W ? 0 : slot + 1;
                 }
             }
-            const unsigned later = __ballot_sync(kFullMask, myrow != r) & ~((2u << i0) - 1u);
-            const int i1 = later ? __ffs(later) - 1 : cnt;
-            for (int i = i0 + h; i < i1; i += S) {
-                const T *s = stg + i * SLOT;
-                if constexpr (F32) {
-                    const uint64_t cx = *reinterpret_cast<const uint64_t *>(s + OCX + 2 * q);
-#pragma unroll
-                    for (int k = 0; k < W; k += 2) {
-                        const ulonglong2 wp = *reinterpret_cast<const ulonglong2 *>(s + 2 * k);
-                        fma2(accp[k], cx, wp.x);
-                        if (k + 1 < W) fma2(accp[k + 1 < W ? k + 1 : k], cx, wp.y);
-                    }
-                } else {
-                    const C cx = *reinterpret_cast<const C *>(s + OCX + 2 * q);
-                    T wy[W];
-                    load_row<W>(s, wy);
-#pragma unroll
-                    for (int k = 0; k < W; ++k) {
-                        accr[k] += cx.x * wy[k];
-                        acci[k] += cx.y * wy[k];
-                    }
-                }
+            const int nb = bbase + 32;                     // prefetch the next batch
+            if (nb + lane < np) {
+                rc = recs[piece + idx[nb + lane]];
+                cv = cin[unpack_word<T>(rc.z)];
             }
-            i0 = i1;
+            bend = bbase + c;
+            __syncwarp();
+        };
+        // Walk the padded rows in blocks of W, so that row r = rb + k lives in the
+        // static slot k: process the points starting at r, then r is complete.
+        int pos = 0;
+        int g = grow0;
+        int k = 0;                                         // slot of row r = r mod W
+#pragma unroll 1
+        for (int r = 0; r < a.p1; ++r) {
+            const int end = r <= a.m1 ? cnt[r] : pos;
+            while (pos < end) {
+                if (pos == bend) stage_next();
+                const int e = min(end, bend);
+                const int ie = e - bbase;
+                int i = pos - bbase + h;
+                for (; i + S < ie; i += 2 * S) {
+                    step(i);
+                    step(i + S);
+                }
+                if (i < ie) step(i);
+                pos = e;
+            }
+#pragma unroll
+            for (int kk = 0; kk < W; ++kk)                 // row r is complete: flush slot k
+                if (kk == k) flush(kk, g);
+            g = g + 1 == a.n1 ? 0 : g + 1;
+            k = k + 1 == W ? 0 : k + 1;
         }
-        __syncwarp();
+        __syncwarp();                                      // idx / cnt reused by the next piece
     }
-#pragma unroll
-    for (int k = 0; k < W; ++k) flush_slot(k, row + k);
 }
 
 // ---------------------------------------------------------------------------
 // Row-sweep SM spreading, 3D (single precision, W <= 8, bins m2 = M2 in {1, 2}).
 // As the 2D sweep: S = 32 / L sub-warps, lane q owns x column q of the padded
 // bin (p0 <= L) and holds the W y rows in reach times all M2 + W z planes in
-// registers.  The records come ordered by (window start row, start plane) from
-// setpts; the points of one (row, plane) group are dealt to the sub-warps, so the first
+// registers.  The points are ordered by (window start row, start plane) as in
+// 2D; the points of one (row, plane) group are dealt to the sub-warps, so the first
 // plane s_z is the same for the whole warp and selects one of M2 + 1 unrolled
 // updates  acc[j][s_z + k] += (c w_x[q - s_x] w_y[j]) w_z[k],  j, k < W.
 // A finished row is summed over the sub-warps and added to the fine grid plane
 // by plane.
 // ---------------------------------------------------------------------------
-template <typename T, int W, int L>
-__host__ __device__ inline size_t sweep3_bytes()
+template <typename T, int W, int M2, int L>
+__host__ __device__ inline size_t sweep3_bytes(int m1)
 {
-    return sizeof(T) * (size_t)32 * sweep3_slot<T, W, L>();
+    return sweep_head((m1 + 1) * (M2 + 1)) + sizeof(T) * (size_t)32 * sweep3_slot<T, W, L>();
 }
 
-// acc[j][O + k] += tu[j] * wzz[k], packed (re, im) pairs
+// acc[j][O + k] += tu[j] * wzz[k], (re, im) pairs
 template <int W, int PZ, int O>
-__device__ __forceinline__ void sweep3_add(uint64_t (&acc)[W][PZ], const uint64_t (&tu)[W],
-                                           const uint64_t (&wzz)[W])
+__device__ __forceinline__ void sweep3_add(float2 (&acc)[W][PZ], const float2 (&tu)[W],
+                                           const float2 (&wzz)[W])
 {
 #pragma unroll
     for (int j = 0; j < W; ++j) {
@@ -627,7 +690,8 @@ __device__ __forceinline__ void sweep3_add(uint64_t (&acc)[W][PZ], const uint64_
 }
 
 template <typename T, int W, int M2, int L>
-__device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, int tr, T *stg)
+__device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, int tr,
+                                                  unsigned char *sm)
 {
     static_assert(sizeof(T) == 4, "the 3D row sweep is single precision");
     using C = typename cplx<T>::type;
@@ -638,6 +702,10 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
     constexpr int OWY = 0, OWZ = 4 * ((W + 1) / 2), OCX = 2 * OWZ;
     const int lane = threadIdx.x & 31, h = lane / L, q = lane % L;
     const int n = sub.z;
+    const int nkeys = (a.m1 + 1) * (M2 + 1);
+    uint16_t *idx = reinterpret_cast<uint16_t *>(sm);
+    int *cnt = reinterpret_cast<int *>(sm + 2 * kSweepCap);
+    T *stg = reinterpret_cast<T *>(sm + sweep_head(nkeys));
 
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
@@ -647,20 +715,19 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
     const bool writer = h == 0 && q < a.p0;
     const int gx = wrap_any(o0 - P + (q < a.p0 ? q : 0), a.n0);
     const int row0 = o1 - P, plane0 = o2 - P;
-    uint64_t acc[W][PZ];                                   // (re, im) of row j, plane k
+    float2 acc[W][PZ];                                     // (re, im) of row j, plane k
 #pragma unroll
     for (int j = 0; j < W; ++j)
 #pragma unroll
-        for (int k = 0; k < PZ; ++k) acc[j][k] = 0ull;
+        for (int k = 0; k < PZ; ++k) acc[j][k] = make_float2(0.f, 0.f);
     int row = 0;
 
-    auto flush_row = [&](int r_rel, const uint64_t (&v)[PZ]) {
+    auto flush_row = [&](int r_rel, const float2 (&v)[PZ]) {
         float vr[PZ], vi[PZ];
 #pragma unroll
         for (int k = 0; k < PZ; ++k) {
-            const float2 f = unpack2(v[k]);
-            vr[k] = f.x;
-            vi[k] = f.y;
+            vr[k] = v[k].x;
+            vi[k] = v[k].y;
 #pragma unroll
             for (int o = L; o < 32; o <<= 1) {
                 vr[k] += __shfl_xor_sync(kFullMask, vr[k], o);
@@ -680,16 +747,20 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
 
     R rc;
     C cv;
+    int piece = 0, np = 0;
     auto fetch = [&](int base) {
-        if (base + lane < n) {
-            const int64_t pos = sub.y + base + lane;
+        if (base + lane < np) {
+            const int64_t pos = sub.y + piece + idx[base + lane];
             rc = a.recs[pos];
             cv = cin[a.order[pos]];
         }
     };
+    for (piece = 0; piece < n; piece += kSweepCap) {
+    np = min(kSweepCap, n - piece);
+    sweep_row_order<T, M2 + 1>(a.recs + sub.y + piece, np, nkeys, idx, cnt);
     fetch(0);
-    for (int base = 0; base < n; base += 32) {
-        const int cnt = min(32, n - base);
+    for (int base = 0; base < np; base += 32) {
+        const int cnt = min(32, np - base);
         int mykey = 0x7fffffff;
         if (lane < cnt) {
             const uint32_t pk = unpack_word<T>(rc.w);
@@ -712,7 +783,7 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
             store_dup_row<W>(s + OWY, vy);
             store_dup_row<W>(s + OWZ, vz);
         }
-        if (base == 0) row = __shfl_sync(kFullMask, mykey, 0) / (M2 + 1);
+        if (base == 0 && piece == 0) row = __shfl_sync(kFullMask, mykey, 0) / (M2 + 1);
         fetch(base + 32);
         __syncwarp();
         int i0 = 0;
@@ -724,7 +795,7 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
                 for (int j = 0; j < W; ++j) {
                     flush_row(row + j, acc[j]);
 #pragma unroll
-                    for (int k = 0; k < PZ; ++k) acc[j][k] = 0ull;
+                    for (int k = 0; k < PZ; ++k) acc[j][k] = make_float2(0.f, 0.f);
                 }
                 row = rrow;
             }
@@ -735,7 +806,7 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
 #pragma unroll
                     for (int k = 0; k < PZ; ++k) acc[j][k] = acc[j + 1][k];
 #pragma unroll
-                for (int k = 0; k < PZ; ++k) acc[W - 1][k] = 0ull;
+                for (int k = 0; k < PZ; ++k) acc[W - 1][k] = make_float2(0.f, 0.f);
                 ++row;
             }
             const unsigned later = __ballot_sync(kFullMask, mykey != r) & ~((2u << i0) - 1u);
@@ -743,17 +814,17 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
             const int sz = r - rrow * (M2 + 1);             // the group's first plane
             for (int i = i0 + h; i < i1; i += S) {
                 const T *s = stg + i * SLOT;
-                const uint64_t cx = *reinterpret_cast<const uint64_t *>(s + OCX + 2 * q);
-                uint64_t tu[W], wzz[W];
+                const float2 cx = *reinterpret_cast<const float2 *>(s + OCX + 2 * q);
+                float2 tu[W], wzz[W];
 #pragma unroll
                 for (int k = 0; k < W; k += 2) {
-                    const ulonglong2 y2 = *reinterpret_cast<const ulonglong2 *>(s + OWY + 2 * k);
-                    const ulonglong2 z2 = *reinterpret_cast<const ulonglong2 *>(s + OWZ + 2 * k);
-                    tu[k] = mul2(cx, y2.x);
-                    wzz[k] = z2.x;
+                    const float4 y2 = *reinterpret_cast<const float4 *>(s + OWY + 2 * k);
+                    const float4 z2 = *reinterpret_cast<const float4 *>(s + OWZ + 2 * k);
+                    tu[k] = mul2(cx, make_float2(y2.x, y2.y));
+                    wzz[k] = make_float2(z2.x, z2.y);
                     if (k + 1 < W) {
-                        tu[k + 1 < W ? k + 1 : k] = mul2(cx, y2.y);
-                        wzz[k + 1 < W ? k + 1 : k] = z2.y;
+                        tu[k + 1 < W ? k + 1 : k] = mul2(cx, make_float2(y2.z, y2.w));
+                        wzz[k + 1 < W ? k + 1 : k] = make_float2(z2.z, z2.w);
                     }
                 }
                 if (sz == 0)
@@ -767,6 +838,7 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
         }
         __syncwarp();
     }
+    }
 #pragma unroll
     for (int j = 0; j < W; ++j) flush_row(row + j, acc[j]);
 }
@@ -775,7 +847,7 @@ template <typename T, int W, int M2, int L>
 __device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, int tr,
                                                    unsigned char *sm)
 {
-    spread_sweep3_sub<T, W, M2, L>(a, a.subprob[sp], tr, reinterpret_cast<T *>(sm));
+    spread_sweep3_sub<T, W, M2, L>(a, a.subprob[sp], tr, sm);
 }
 
 template <typename T, int W, int M2, int L>
@@ -797,11 +869,11 @@ template <typename T, int W, int L>
 __device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, int tr,
                                                    unsigned char *sm)
 {
-    spread_sweep2_sub<T, W, L>(a, a.subprob[sp], tr, reinterpret_cast<T *>(sm));
+    spread_sweep2_sub<T, W, L>(a, a.subprob[sp], tr, sm);
 }
 
 template <typename T, int W, int L>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 spread_sweep2_kernel(KArgs<T> a, int warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1077,33 +1149,66 @@ __device__ __forceinline__ void interp_lane_item(const KArgs<T> &a, int sp, int 
     if (STAGED) __syncthreads();
 }
 
-// 2D, one warp per work item: the warp stages its own padded bin (no CTA
-// barriers, so many subproblems are in flight per SM) and its lanes take the
-// subproblem's points as above (2D records carry their point's index).
+// Asynchronous global -> shared copies (cp.async, sm_80+): the data land in
+// shared memory without passing through registers, and a warp can compute on
+// one buffer while the next one is in flight.
+__device__ __forceinline__ void cp_async_cplx(float2 *dst, const float2 *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_cplx(double2 *dst, const double2 *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// 2D interpolation, one warp per work item (no CTA barriers, so many
+// subproblems are in flight per SM).  interp2_stage issues the copies of the
+// work item's padded bin into a warp-private tile (row by row, periodic wrap);
+// interp2_points then has every lane take points of the subproblem as above:
+// the 2D records carry their point's index, and the next record is loaded
+// while the current point is computed.
 template <typename T, int W>
-__device__ __forceinline__ void interp_warp2_item(const KArgs<T> &a, int sp, int tr,
-                                                  typename cplx<T>::type *tile)
+__device__ __forceinline__ void interp2_stage(const KArgs<T> &a, int sp, int tr,
+                                              typename cplx<T>::type *tile)
 {
     using C = typename cplx<T>::type;
-    using R = typename rec4<T>::type;
     const int P = pad_lo(W);
     const int lane = threadIdx.x & 31;
     const int4 sub = a.subprob[sp];
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
     const C *grid = a.grid + (int64_t)tr * a.nftot;
-    C *cout = a.cout + (int64_t)tr * a.M;
-    for (int rx = lane; rx < a.p0; rx += 32) {            // stage the padded bin, row by row
+    for (int rx = lane; rx < a.p0; rx += 32) {
         const C *src = grid + wrap_any(o0 - P + rx, a.n0);
-#pragma unroll 4
-        for (int ry = 0; ry < a.p1; ++ry)
-            tile[ry * a.p0 + rx] = src[(int64_t)wrap_any(o1 - P + ry, a.n1) * a.n0];
+        int gy = wrap_any(o1 - P, a.n1);
+        for (int ry = 0; ry < a.p1; ++ry) {
+            cp_async_cplx(tile + ry * a.p0 + rx, src + (int64_t)gy * a.n0);
+            gy = gy + 1 == a.n1 ? 0 : gy + 1;
+        }
     }
-    __syncwarp();
-    // records in execution order (rows, then columns): neighbouring lanes read
-    // neighbouring cells of the tile
-    for (int k = lane; k < sub.z; k += 32) {
-        const R rc = a.recs[sub.y + k];
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void interp2_points(const KArgs<T> &a, int sp, int tr,
+                                               const typename cplx<T>::type *tile)
+{
+    using C = typename cplx<T>::type;
+    using R = typename rec4<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int4 sub = a.subprob[sp];
+    C *cout = a.cout + (int64_t)tr * a.M;
+    const R *recs = a.recs + sub.y;
+    const int np = sub.z;
+    R rn;
+    if (lane < np) rn = recs[lane];
+    for (int k = lane; k < np; k += 32) {
+        const R rc = rn;
+        if (k + 32 < np) rn = recs[k + 32];
         const int j = (int)unpack_word<T>(rc.z);
         const uint32_t pk = unpack_word<T>(rc.w);
         const int sx = pk & 1023u, sy = (pk >> 10) & 1023u;
@@ -1112,22 +1217,18 @@ __device__ __forceinline__ void interp_warp2_item(const KArgs<T> &a, int sp, int
         kernel_row<T, W>(a, rc.y, wy);
         C o;
         if constexpr (sizeof(T) == 4) {
-            // packed (re, im) sums: one f32x2 FMA per cell
-            uint64_t wxx[W];
-#pragma unroll
-            for (int ix = 0; ix < W; ++ix) wxx[ix] = pack2(wx[ix], wx[ix]);
-            uint64_t acc = 0ull;
+            // (re, im) sums: one f32x2 FMA per cell
+            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int iy = 0; iy < W; ++iy) {
-                const uint64_t *t = reinterpret_cast<const uint64_t *>(tile + (sy + iy) * a.p0 + sx);
-                uint64_t yv = 0ull;
+                const float2 *t = reinterpret_cast<const float2 *>(tile + (sy + iy) * a.p0 + sx);
+                float2 yv = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int ix = 0; ix < W; ++ix) fma2(yv, t[ix], wxx[ix]);
-                fma2(acc, yv, pack2(wy[iy], wy[iy]));
+                for (int ix = 0; ix < W; ++ix) fma2(yv, t[ix], make_float2(wx[ix], wx[ix]));
+                fma2(acc, yv, make_float2(wy[iy], wy[iy]));
             }
-            const float2 v = unpack2(acc);
-            o.x = v.x;
-            o.y = v.y;
+            o.x = acc.x;
+            o.y = acc.y;
         } else {
             T ar = 0, ai = 0;
 #pragma unroll
@@ -1148,22 +1249,60 @@ __device__ __forceinline__ void interp_warp2_item(const KArgs<T> &a, int sp, int
         }
         cout[j] = o;
     }
-    __syncwarp();
 }
 
+// One work item with its own (not overlapped) staging: the batched form.
+template <typename T, int W>
+__device__ __forceinline__ void interp_warp2_item(const KArgs<T> &a, int sp, int tr,
+                                                  unsigned char *sm)
+{
+    auto *tile = reinterpret_cast<typename cplx<T>::type *>(sm);
+    __syncwarp();
+    interp2_stage<T, W>(a, sp, tr, tile);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    interp2_points<T, W>(a, sp, tr, tile);
+}
+
+// Shared memory of one warp of the 2D interpolation: `buffers` padded bins of
+// tile_elems cells.
+template <typename T>
+__host__ __device__ inline size_t interp2_warp_bytes(int tile_elems, int buffers)
+{
+    return sizeof(typename cplx<T>::type) * (size_t)tile_elems * buffers;
+}
+
+// Single plan: each warp walks its work items with two tiles, copying the next
+// item's padded bin while it interpolates at the current one's points.
 template <typename T, int W>
 __global__ void __launch_bounds__(256)
 interp_warp2_kernel(KArgs<T> a, int tile_elems)
 {
+    using C = typename cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
-    auto *tile = reinterpret_cast<typename cplx<T>::type *>(smem_raw) + (size_t)warp * tile_elems;
+    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)warp * 2 * tile_elems;
     const int per_cta = blockDim.x >> 5;
     const int nsp = *a.nsub;
     const int64_t nwork = (int64_t)nsp * a.ntransf;
-    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
-         wi += (int64_t)gridDim.x * per_cta)
-        interp_warp2_item<T, W>(a, (int)(wi % nsp), (int)(wi / nsp), tile);
+    const int64_t stride = (int64_t)gridDim.x * per_cta;
+    int64_t wi = (int64_t)blockIdx.x * per_cta + warp;
+    if (wi < nwork) interp2_stage<T, W>(a, (int)(wi % nsp), (int)(wi / nsp), buf);
+    cp_async_commit();
+    int cur = 0;
+    for (; wi < nwork; wi += stride) {
+        const int64_t nx = wi + stride;
+        if (nx < nwork)
+            interp2_stage<T, W>(a, (int)(nx % nsp), (int)(nx / nsp), buf + (cur ^ 1) * tile_elems);
+        cp_async_commit();
+        cp_async_wait<1>();                                // the current tile has landed
+        __syncwarp();
+        interp2_points<T, W>(a, (int)(wi % nsp), (int)(wi / nsp), buf + cur * tile_elems);
+        __syncwarp();                                      // before the tile is refilled
+        cur ^= 1;
+    }
+    cp_async_wait<0>();
 }
 
 template <typename T, int DIM, int W, bool STAGED>
@@ -1333,14 +1472,14 @@ spread_sweep3_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__r
 template <typename T, int W>
 __global__ void __launch_bounds__(256)
 interp_warp2_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
-                          int nplans, int tile_elems)
+                          int nplans, int warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
-    const size_t slot = args_slot<T>() + sizeof(typename cplx<T>::type) * (size_t)tile_elems;
+    const size_t slot = args_slot<T>() + (size_t)warp_bytes;
     unsigned char *base = smem_raw + (size_t)warp * slot;
     KArgs<T> *cache = reinterpret_cast<KArgs<T> *>(base);
-    auto *tile = reinterpret_cast<typename cplx<T>::type *>(base + args_slot<T>());
+    unsigned char *sm = base + args_slot<T>();
     const int per_cta = blockDim.x >> 5;
     int cached = -1;
     const int64_t nwork = workoff[nplans];
@@ -1351,7 +1490,7 @@ interp_warp2_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__re
         const KArgs<T> &a = *cache;
         const int64_t local = wi - workoff[pl];
         const int nsp = *a.nsub;
-        interp_warp2_item<T, W>(a, (int)(local % nsp), (int)(local / nsp), tile);
+        interp_warp2_item<T, W>(a, (int)(local % nsp), (int)(local / nsp), sm);
     }
 }
 
@@ -1432,7 +1571,7 @@ KArgs<T> make_args(const Plan &p)
 {
     KArgs<T> a;
     a.recs = reinterpret_cast<const typename rec4<T>::type *>(p.recs);
-    a.order = p.order;
+    a.order = p.perm;                              // records are in t order
     a.subprob = p.subprob;
     a.nsub = p.nsub;
     a.xyz0 = reinterpret_cast<const T *>(p.xyz_copy[0]);
@@ -1479,7 +1618,7 @@ inline int persistent_grid(const Plan &p, K kernel, int threads, size_t smem)
 template <typename T, int W, int L>
 bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
 {
-    const size_t warp_bytes = sweep_bytes<T, W, L>();
+    const size_t warp_bytes = sweep_bytes<T, W, L>(a.m1);
     int nw = threads / 32;
     while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
     if (nw < 2) return false;
@@ -1497,7 +1636,7 @@ bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
 template <typename T, int W, int M2, int L>
 bool launch_sweep3(Plan &p, const KArgs<T> &a, cudaError_t *err)
 {
-    const size_t warp_bytes = sweep3_bytes<T, W, L>();
+    const size_t warp_bytes = sweep3_bytes<T, W, M2, L>(a.m1);
     int nw = 4;
     while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
     if (nw < 2) return false;
@@ -1569,7 +1708,7 @@ cudaError_t interp_w(Plan &p, void *c)
     if (p.method == NUFFT_METHOD_SM && DIM == 2) {
         // one padded bin per warp, as many warps per CTA as shared memory allows
         const int tile = a.p0 * a.p1;
-        const size_t per_warp = sizeof(typename cplx<T>::type) * (size_t)tile;
+        const size_t per_warp = interp2_warp_bytes<T>(tile, 2);
         int nw = threads / 32;
         while (nw > 1 && (size_t)nw * per_warp > (size_t)p.smem_optin) --nw;
         if ((size_t)nw * per_warp <= (size_t)p.smem_optin) {
@@ -1615,7 +1754,7 @@ cudaError_t spread_multi_w(const MultiLaunch &ml)
     count_launch();
     if (ml.method == NUFFT_METHOD_SM && ml.variant > 0) {
         if constexpr (DIM == 2) {
-            const size_t wb = sweep_bytes<T, W, 32>();
+            const size_t wb = sweep_bytes<T, W, 32>(ml.m1max);
             const size_t per = args_slot<T>() + wb;
             int nw = 8;
             while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
@@ -1631,7 +1770,7 @@ cudaError_t spread_multi_w(const MultiLaunch &ml)
             if (ml.variant == 16) return launch(spread_sweep2_multi_kernel<T, W, 16>, (int)wb);
             return launch(spread_sweep2_multi_kernel<T, W, 32>, (int)wb);
         } else if constexpr (sizeof(T) == 4 && W <= 8) {
-            const size_t wb = sweep3_bytes<T, W, 32>();
+            const size_t wb = sweep3_bytes<T, W, 2, 32>(ml.m1max);
             const size_t per = args_slot<T>() + wb;
             int nw = 4;
             while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
@@ -1672,7 +1811,8 @@ cudaError_t interp_multi_w(const MultiLaunch &ml)
     const auto *args = reinterpret_cast<const KArgs<T> *>(ml.args);
     count_launch();
     if (ml.method == NUFFT_METHOD_SM && DIM == 2) {
-        const size_t per = args_slot<T>() + sizeof(C) * (size_t)ml.tile;
+        const size_t wb = interp2_warp_bytes<T>(ml.tile, 1);
+        const size_t per = args_slot<T>() + wb;
         int nw = 8;
         while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
         if ((size_t)nw * per <= ml.smem_optin) {
@@ -1680,7 +1820,7 @@ cudaError_t interp_multi_w(const MultiLaunch &ml)
             auto k = interp_warp2_multi_kernel<T, W>;
             if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
             k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
-                args, ml.workoff, ml.nplans, ml.tile);
+                args, ml.workoff, ml.nplans, (int)wb);
             return cudaGetLastError();
         }
     }
