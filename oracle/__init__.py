@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the 2D/3D type 1 and type 2 NUFFT of arXiv 2102.08463.
+"""FP64 CPU oracle for the 1D/2D/3D type 1 and type 2 NUFFT of arXiv 2102.08463
+(and the exact type 3 sum).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import this package; the GPU library never
@@ -9,7 +10,11 @@ against a tight-tolerance CPU reference):
 
 * O1 -- exact sums, Eq. (2d1) and Eq. (2d2), in FP64 with compensated phases and
   compensated summation (``direct_type1`` / ``direct_type2``); optionally only a
-  sampled subset of modes or targets.
+  sampled subset of modes or targets.  ``direct_type3`` is the same sum at real
+  (nonuniform) frequencies: the type 3 transform, which the paper defines by
+  reference only and lists as future work, so its oracle is the definition.
+  1D is the d = 1 case of every sum and of the three-step algorithm (the paper
+  gives the method per dimension, Sec. 3; 1D is also listed as future work).
 * O2 -- the plain three-step algorithm of Sec. 3.1 / 3.2 in FP64
   (``nufft_type1`` / ``nufft_type2``): C spreading / interpolation loops,
   ``numpy.fft`` as the FFT step, and the deconvolution factors of Sec. 3.1 step 3
@@ -65,6 +70,8 @@ def _load():
                                          P, I64, P, P]
         lib.orc_direct_type2.argtypes = [ctypes.c_int, I64, P, P, P, P, ctypes.c_int,
                                          P, I64, P, P]
+        lib.orc_direct_type3.argtypes = [ctypes.c_int, I64, P, P, P, P, ctypes.c_int,
+                                         I64, P, P, P, P]
         lib.orc_spread.argtypes = [ctypes.c_int, I64, P, P, P, P, P, ctypes.c_int,
                                    ctypes.c_double, P]
         lib.orc_interp.argtypes = [ctypes.c_int, I64, P, P, P, P, P, ctypes.c_int,
@@ -214,6 +221,11 @@ def _coords(pts):
     return pts, M
 
 
+def _y(pts):
+    """The second coordinate array, or None in 1D."""
+    return pts[1] if len(pts) >= 2 else None
+
+
 def direct_type1(pts, c, N, iflag=+1, modes=None):
     """f_k = sum_j c_j exp(i iflag k.x_j) (Eq. 2d1 with sign iflag).
 
@@ -233,7 +245,7 @@ def direct_type1(pts, c, N, iflag=+1, modes=None):
         nk = kl.shape[0]
     f = np.zeros(nk, dtype=np.complex128)
     z = pts[2] if dim == 3 else None
-    _load().orc_direct_type1(dim, M, _ptr(pts[0]), _ptr(pts[1]), _ptr(z), _ptr(c),
+    _load().orc_direct_type1(dim, M, _ptr(pts[0]), _ptr(_y(pts)), _ptr(z), _ptr(c),
                              int(iflag), _ptr(Nv), nk, _ptr(kl), _ptr(f))
     if modes is None:
         return f.reshape(tuple(reversed(tuple(int(v) for v in N))))
@@ -259,9 +271,27 @@ def direct_type2(pts, f, iflag=+1, targets=None):
         nt = jl.shape[0]
     c = np.zeros(nt, dtype=np.complex128)
     z = pts[2] if dim == 3 else None
-    _load().orc_direct_type2(dim, M, _ptr(pts[0]), _ptr(pts[1]), _ptr(z), _ptr(f),
+    _load().orc_direct_type2(dim, M, _ptr(pts[0]), _ptr(_y(pts)), _ptr(z), _ptr(f),
                              int(iflag), _ptr(Nv), nt, _ptr(jl), _ptr(c))
     return c
+
+
+def direct_type3(pts, c, freqs, iflag=+1):
+    """f_k = sum_j c_j exp(i iflag s_k.x_j) at real frequencies s_k: the type 3
+    (nonuniform to nonuniform) transform the paper names as future work, by its
+    definition.  pts and freqs: lists of d arrays (M and K entries)."""
+    pts, M = _coords(pts)
+    fr, K = _coords(freqs)
+    dim = len(pts)
+    if len(fr) != dim:
+        raise ValueError("points and frequencies must have the same dimension")
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.complex128))
+    f = np.zeros(K, dtype=np.complex128)
+    z = pts[2] if dim == 3 else None
+    u = fr[2] if dim == 3 else None
+    _load().orc_direct_type3(dim, M, _ptr(pts[0]), _ptr(_y(pts)), _ptr(z), _ptr(c), int(iflag),
+                             K, _ptr(fr[0]), _ptr(_y(fr)), _ptr(u), _ptr(f))
+    return f
 
 
 # ---------------------------------------------------------------------------
@@ -275,7 +305,7 @@ def spread(pts, c, n, w, beta):
     nv = np.asarray(n, dtype=np.int64)
     b = np.zeros(tuple(reversed(tuple(int(v) for v in n))), dtype=np.complex128)
     z = pts[2] if dim == 3 else None
-    _load().orc_spread(dim, M, _ptr(pts[0]), _ptr(pts[1]), _ptr(z), _ptr(c), _ptr(nv),
+    _load().orc_spread(dim, M, _ptr(pts[0]), _ptr(_y(pts)), _ptr(z), _ptr(c), _ptr(nv),
                        int(w), float(beta), _ptr(b))
     return b
 
@@ -289,7 +319,7 @@ def interp(pts, b, w, beta):
     nv = np.asarray(n, dtype=np.int64)
     c = np.zeros(M, dtype=np.complex128)
     z = pts[2] if dim == 3 else None
-    _load().orc_interp(dim, M, _ptr(pts[0]), _ptr(pts[1]), _ptr(z), _ptr(b), _ptr(nv),
+    _load().orc_interp(dim, M, _ptr(pts[0]), _ptr(_y(pts)), _ptr(z), _ptr(b), _ptr(nv),
                        int(w), float(beta), _ptr(c))
     return c
 
@@ -307,8 +337,11 @@ def _mode_index(N, n):
 
 
 def _correction(P, nquad=200):
+    """Separable correction p_k on the (N_d, .., N_1) mode array (Sec. 3.1 step 3)."""
     facs = [correction_1d(Ni, ni, P.w, P.beta, nquad) for Ni, ni in zip(P.N, P.n)]
-    out = facs[0][None, :] * facs[1][:, None]
+    out = facs[0]
+    if P.dim >= 2:
+        out = out[None, :] * facs[1][:, None]
     if P.dim == 3:
         out = out[None, :, :] * facs[2][:, None, None]
     return out
@@ -361,7 +394,7 @@ def binsort(pts, n, m):
     counts = np.zeros(max(nbins, 1), dtype=np.int64)
     t = np.zeros(M, dtype=np.int64)
     z = pts[2] if dim == 3 else None
-    _load().orc_binsort(dim, M, _ptr(pts[0]), _ptr(pts[1]), _ptr(z), _ptr(nv), _ptr(mv),
+    _load().orc_binsort(dim, M, _ptr(pts[0]), _ptr(_y(pts)), _ptr(z), _ptr(nv), _ptr(mv),
                         _ptr(binidx), _ptr(counts), _ptr(t))
     return binidx, counts[:nbins], t
 

@@ -1,6 +1,6 @@
 /*
- * nufft_oracle.c -- plain, slow FP64 CPU reference for the 2D/3D type 1 and
- * type 2 NUFFT of Shih et al., "cuFINUFFT: a load-balanced GPU library for
+ * nufft_oracle.c -- plain, slow FP64 CPU reference for the 1D/2D/3D type 1,
+ * type 2 (and exact type 3) NUFFT of Shih et al., "cuFINUFFT: a load-balanced GPU library for
  * general-purpose nonuniform FFTs" (arXiv 2102.08463).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the GPU library links, includes or
@@ -12,6 +12,8 @@
  *   orc_es_kernel      ES kernel phi_beta (Sec. 3, Eq. "es").
  *   orc_direct_type1   exact type 1 sum (Eq. 2d1, extended to 3D as Sec. 1 says).
  *   orc_direct_type2   exact type 2 sum (Eq. 2d2).
+ *   orc_direct_type3   exact type 3 sum (nonuniform to nonuniform; the third
+ *                      type, which the paper lists as future work).
  *   orc_spread         type 1 step 1, spreading with the periodised kernel (Sec. 3.1).
  *   orc_interp         type 2 step 3, interpolation (Sec. 3.2).
  *   orc_cells          fixed-point bin rule for the bin-sort (Sec. 4.1, GM-sort).
@@ -167,6 +169,36 @@ void orc_direct_type2(int dim, int64_t M, const double *x, const double *y,
     }
 }
 
+/*
+ * Exact type 3 sum with exponent sign iflag, at real frequencies (s_k, t_k, u_k):
+ *   f_k = sum_j c_j exp(i*iflag*(s_k x_j + t_k y_j + u_k z_j)),  k < nk.
+ * The same compensated phase and sum as type 1, with non-integer frequencies.
+ */
+void orc_direct_type3(int dim, int64_t M, const double *x, const double *y,
+                      const double *z, const double *c, int iflag, int64_t nk,
+                      const double *s, const double *t, const double *u, double *f)
+{
+    const double *xs[3] = {x, y, z};
+    const double *ks[3] = {s, t, u};
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nk; ++q) {
+        double k[3] = {0, 0, 0};
+        for (int i = 0; i < dim; ++i) k[i] = ks[i][q];
+        acc_t ar = {0, 0}, ai = {0, 0};
+        for (int64_t j = 0; j < M; ++j) {
+            double xv[3];
+            for (int i = 0; i < dim; ++i) xv[i] = xs[i][j];
+            double er, ei;
+            phase_exp(dim, k, xv, (double)iflag, &er, &ei);
+            double cr = c[2 * j], ci = c[2 * j + 1];
+            acc_add(&ar, cr * er - ci * ei);
+            acc_add(&ai, cr * ei + ci * er);
+        }
+        f[2 * q] = acc_val(&ar);
+        f[2 * q + 1] = acc_val(&ai);
+    }
+}
+
 /* ---------------------------------------------------------------------------
  * Spreading and interpolation, Sec. 3.1 step 1 and Sec. 3.2 step 3.
  * psi(x) = prod_i phi_beta(x_i / alpha_i), alpha_i = w pi / n_i, periodised.
@@ -201,7 +233,7 @@ void orc_spread(int dim, int64_t M, const double *x, const double *y,
                 double beta, double *b)
 {
     const double *xs[3] = {x, y, z};
-    int64_t nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+    int64_t nn[3] = {n[0], dim >= 2 ? n[1] : 1, dim == 3 ? n[2] : 1};
     int64_t ntot = nn[0] * nn[1] * nn[2];
     memset(b, 0, sizeof(double) * 2 * (size_t)ntot);
     int slow = dim - 1;
@@ -228,17 +260,18 @@ void orc_spread(int dim, int64_t M, const double *x, const double *y,
             for (int d = 0; d < slow; ++d)
                 window_1d(xs[d][j], nn[d], w, beta, &l0[d], wt + d * w);
             double cr = c[2 * j], ci = c[2 * j + 1];
-            int wzn = dim == 3 ? w : 1;
+            int wzn = dim == 3 ? w : 1, wyn = dim >= 2 ? w : 1;
             for (int iz = 0; iz < wzn; ++iz) {
                 int64_t lz = dim == 3 ? wrap(l0[2] + iz, nn[2]) : 0;
                 double vz = dim == 3 ? wz[iz] : 1.0;
                 if (dim == 3 && !(lz >= r0 && lz < r1)) continue;
-                for (int iy = 0; iy < w; ++iy) {
-                    int64_t ly = wrap(l0[1] + iy, nn[1]);
+                for (int iy = 0; iy < wyn; ++iy) {
+                    int64_t ly = dim >= 2 ? wrap(l0[1] + iy, nn[1]) : 0;
                     if (dim == 2 && !(ly >= r0 && ly < r1)) continue;
-                    double vyz = vz * wy[iy];
+                    double vyz = dim >= 2 ? vz * wy[iy] : vz;
                     for (int ix = 0; ix < w; ++ix) {
                         int64_t lx = wrap(l0[0] + ix, nn[0]);
+                        if (dim == 1 && !(lx >= r0 && lx < r1)) continue;
                         double v = vyz * wx[ix];
                         int64_t cell = lx + nn[0] * (ly + nn[1] * lz);
                         b[2 * cell] += v * cr;
@@ -260,7 +293,7 @@ void orc_interp(int dim, int64_t M, const double *x, const double *y,
                 double beta, double *c)
 {
     const double *xs[3] = {x, y, z};
-    int64_t nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+    int64_t nn[3] = {n[0], dim >= 2 ? n[1] : 1, dim == 3 ? n[2] : 1};
     #pragma omp parallel
     {
         double *wt = (double *)malloc(sizeof(double) * 3 * (size_t)w);
@@ -270,13 +303,13 @@ void orc_interp(int dim, int64_t M, const double *x, const double *y,
             for (int d = 0; d < dim; ++d)
                 window_1d(xs[d][j], nn[d], w, beta, &l0[d], wt + d * w);
             double sr = 0.0, si = 0.0;
-            int wzn = dim == 3 ? w : 1;
+            int wzn = dim == 3 ? w : 1, wyn = dim >= 2 ? w : 1;
             for (int iz = 0; iz < wzn; ++iz) {
                 int64_t lz = dim == 3 ? wrap(l0[2] + iz, nn[2]) : 0;
                 double vz = dim == 3 ? wt[2 * w + iz] : 1.0;
-                for (int iy = 0; iy < w; ++iy) {
-                    int64_t ly = wrap(l0[1] + iy, nn[1]);
-                    double vyz = vz * wt[w + iy];
+                for (int iy = 0; iy < wyn; ++iy) {
+                    int64_t ly = dim >= 2 ? wrap(l0[1] + iy, nn[1]) : 0;
+                    double vyz = dim >= 2 ? vz * wt[w + iy] : vz;
                     for (int ix = 0; ix < w; ++ix) {
                         int64_t lx = wrap(l0[0] + ix, nn[0]);
                         double v = vyz * wt[ix];

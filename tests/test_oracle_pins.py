@@ -317,3 +317,105 @@ def test_sigma125_width_rule_meets_eps(eps):
     assert e_w <= eps            # the calibrated width reaches the tolerance
     assert e_w1 > e_w            # one cell narrower is measurably worse
     assert oracle.Params(N, eps, 1.25).n == (50, 45)   # 2^a 3^b 5^c >= 1.25 N
+
+
+# ---------------------------------------------------------------------------
+# 1D (the d = 1 case of Eq. 2d1 / 2d2 and of the algorithm of Sec. 3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("iflag", [+1, -1])
+def test_direct_1d_on_grid_points_is_a_dft(iflag):
+    N = 9
+    x = -math.pi + 2 * math.pi * np.arange(N) / N
+    rng = np.random.default_rng(81)
+    c = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    f = oracle.direct_type1([x], c, (N,), iflag)
+    full = np.fft.ifft(c) * N if iflag > 0 else np.fft.fft(c)
+    k = oracle.modes_1d(N)
+    assert np.max(np.abs(f - full[k % N] * (-1.0) ** k)) < 1e-12
+    fm = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    g = np.zeros(N, dtype=complex)
+    g[k % N] = fm * (-1.0) ** k
+    ref = np.fft.fft(g) if iflag > 0 else np.fft.ifft(g) * N
+    assert np.max(np.abs(oracle.direct_type2([x], fm, iflag) - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("iflag", [+1, -1])
+def test_pipeline_1d_tight_matches_direct(iflag):
+    N, M = (33,), 400
+    pts = _pts(1, M, 82)
+    c = wl.strengths(M, 83, np.complex128)
+    f = wl.modes(N, 84, np.complex128)
+    assert oracle.rel_l2(oracle.nufft_type1(pts, c, N, eps=1e-14, iflag=iflag),
+                         oracle.direct_type1(pts, c, N, iflag)) < 1e-13
+    assert oracle.rel_l2(oracle.nufft_type2(pts, f, eps=1e-14, iflag=iflag),
+                         oracle.direct_type2(pts, f, iflag)) < 1e-13
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-10])
+def test_pipeline_1d_error_close_to_eps(eps):
+    N, M = (200,), 3000
+    pts = _pts(1, M, 85)
+    c = wl.strengths(M, 86, np.complex128)
+    e1 = oracle.rel_l2(oracle.nufft_type1(pts, c, N, eps), oracle.direct_type1(pts, c, N))
+    assert eps / 1000 < e1 < 5 * eps
+    f = wl.modes(N, 87, np.complex128)
+    e2 = oracle.rel_l2(oracle.nufft_type2(pts, f, eps), oracle.direct_type2(pts, f))
+    assert eps / 1000 < e2 < 5 * eps
+
+
+def test_spread_interp_1d_transpose_mass_periodicity():
+    n, w = (40,), 7
+    beta = oracle.kernel_beta(w)
+    M = 90
+    pts = _pts(1, M, 88)
+    c = wl.strengths(M, 89, np.complex128)
+    b = wl.modes(n, 90, np.complex128)
+    s = oracle.spread(pts, c, n, w, beta)
+    i = oracle.interp(pts, b, w, beta)
+    assert abs(np.vdot(b, s) - np.vdot(i, c)) < 1e-12 * np.abs(c).sum()
+    per_axis = oracle.phihat(np.array([0.0]), beta)[0] * w / 2.0
+    assert abs(s.sum() - c.sum() * per_axis) < 1e-5 * abs(c.sum()) * per_axis
+    s2 = oracle.spread([pts[0] - 4 * math.pi], c, n, w, beta)
+    assert np.max(np.abs(s2 - s)) < 1e-12
+    # a single point: its w weights, one per cell of its window, and nothing else
+    one = oracle.spread([np.array([0.1])], np.array([1.0 + 0j]), n, w, beta)
+    assert np.count_nonzero(one) == w
+
+
+# ---------------------------------------------------------------------------
+# type 3 exact sum (nonuniform frequencies)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_direct_type3_brute_force_and_integer_frequencies(dim):
+    M, K = 23, 17
+    pts = _pts(dim, M, 91 + dim)
+    c = wl.strengths(M, 92, np.complex128)
+    rng = np.random.default_rng(93)
+    s = [rng.uniform(-20, 20, K) for _ in range(dim)]
+    f = oracle.direct_type3(pts, c, s, +1)
+    phase = sum(np.multiply.outer(s[d], pts[d]) for d in range(dim))
+    ref = np.exp(1j * phase) @ c
+    assert np.max(np.abs(f - ref)) < 1e-11 * np.abs(c).sum()
+    assert np.max(np.abs(oracle.direct_type3(pts, c, s, -1) - np.exp(-1j * phase) @ c)) \
+        < 1e-11 * np.abs(c).sum()
+    # at the integer frequencies of I_N it is the type 1 sum
+    N = (5, 4, 3)[:dim]
+    k = np.meshgrid(*[oracle.modes_1d(n) for n in reversed(N)], indexing="ij")
+    kk = [k[dim - 1 - d].ravel().astype(float) for d in range(dim)]
+    f1 = oracle.direct_type1(pts, c, N, +1).ravel()
+    assert np.max(np.abs(oracle.direct_type3(pts, c, kk, +1) - f1)) < 1e-13 * np.abs(c).sum()
+
+
+def test_direct_type3_shift_is_a_modulation():
+    # s -> s + d multiplies each term by e^{i d.x_j}: type 3 at s + d is type 3 at s
+    # of the modulated strengths c_j e^{i d.x_j}
+    M, K = 40, 11
+    pts = _pts(2, M, 94)
+    c = wl.strengths(M, 95, np.complex128)
+    rng = np.random.default_rng(96)
+    s = [rng.uniform(-50, 50, K), rng.uniform(-50, 50, K)]
+    d = (0.37, -1.9)
+    a = oracle.direct_type3(pts, c, [s[0] + d[0], s[1] + d[1]])
+    cm = c * np.exp(1j * (d[0] * pts[0] + d[1] * pts[1]))
+    b = oracle.direct_type3(pts, cm, s)
+    assert np.max(np.abs(a - b)) < 1e-12 * np.abs(c).sum()
