@@ -95,8 +95,9 @@ void nufft_default_opts(nufft_opts *opts);
 /*
  * Create a plan (Sec. 1.1 "plan"; parameters of Sec. 3).
  *   type    1 or 2.
- *   dim     2 or 3.
- *   nmodes  dim entries N1, N2 (, N3), each >= 1.
+ *   dim     1, 2 or 3 (1D is the d = 1 case of Sec. 3, which the paper lists as
+ *           future work: bins of m1 cells, the same three methods).
+ *   nmodes  dim entries N1 (, N2 (, N3)), each >= 1.
  *   iflag   +1 or -1: sign of the type 1 exponent (type 2 uses the opposite).
  *   ntransf number of strength / coefficient vectors per execute (>= 1).
  *   eps     requested relative tolerance; kernel width w = ceil(log10(1/eps)) + 1
@@ -115,12 +116,13 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
 
 /*
  * Set the nonuniform points (Sec. 1.1 "setup"; bin-sort of Sec. 4.1).
- * Computes each point's fine-grid cell, bins of m1 x m2 (x m3) cells with x
+ * Computes each point's fine-grid cell, bins of m1 (x m2 (x m3)) cells with x
  * fastest, the permutation t listing points bin by bin (increasing original
  * index inside a bin, unless the plan was made with opts.unordered_bins), the
  * subproblem list (runs of at most M_sub points of one bin) and packed
  * per-point kernel offsets.
- * M = 0 is allowed.  x, y, z: device arrays of M reals (z NULL in 2D).
+ * M = 0 is allowed.  x, y, z: device arrays of M reals (z NULL in 2D; y and z
+ * NULL in 1D).
  */
 int nufft_setpts(nufft_plan plan, int64_t M, const void *x, const void *y, const void *z);
 
@@ -220,7 +222,8 @@ int nufft_fma_peak(int prec, double *tflops, void *stream);
  * The paper hand-tunes its tiles for its own GPU (Sec. 4.1 remark).  This times
  * candidate tiles -- method (SM, GM-sort, GM), bin sizes, M_sub and threads per
  * CTA -- for one problem on the caller's data and returns the fastest execute.
- *   type ... prec, base   as nufft_makeplan (base may be NULL; its stream is used).
+ *   type ... prec, base   as nufft_makeplan (base may be NULL; its stream is used);
+ *                         dim 2 or 3 (1D plans keep their default tiles).
  *   M, x, y, z            points (device), M >= 1.
  *   c, f                  device arrays of the plan's shapes; overwritten.
  *   reps                  timed executes per candidate (median taken), >= 1.

@@ -558,7 +558,7 @@ class Plan:
     """A plan bound to torch's current CUDA stream (or an explicit one).
 
     Plan(type, N, eps, iflag=+1, ntransf=1, prec=-1, method="auto", ...)
-    N is (N1, N2) or (N1, N2, N3).  Arrays: x, y, z real tensors of the plan
+    N is (N1,), (N1, N2) or (N1, N2, N3).  Arrays: x, y, z real tensors of the plan
     precision; c complex (ntransf, M) / (M,); f complex ([ntransf,] N3, N2, N1).
     """
 
@@ -595,10 +595,10 @@ class Plan:
         self.M = 0
         self._pts = None
 
-    def setpts(self, x, y, z=None):
+    def setpts(self, x, y=None, z=None):
         M = x.shape[0]
         rd = self.real_dtype
-        setpts(self.handle, M, _dptr(x, rd, "x"), _dptr(y, rd, "y"),
+        setpts(self.handle, M, _dptr(x, rd, "x"), _dptr(y, rd, "y") if self.dim >= 2 else None,
                _dptr(z, rd, "z") if self.dim == 3 else None)
         self.M = M
         self._pts = (x, y, z)   # keep alive until the stream has consumed them
@@ -623,7 +623,7 @@ class Plan:
         execute(self.handle, _dptr(c, cd, "c"), _dptr(f, cd, "f"))
         return c
 
-    def execute_host(self, x, y, z=None, c=None, f=None, sync=True):
+    def execute_host(self, x, y=None, z=None, c=None, f=None, sync=True):
         """nufft_execute_host on host (CPU) tensors: set the points and execute with
         the copies inside the call.  Type 1 reads c and returns f (new, or into f);
         type 2 reads f and returns c.  Pinned tensors let the copies overlap the
@@ -642,7 +642,8 @@ class Plan:
                 f = torch.empty(shp_f, dtype=cd, pin_memory=pin)
         elif c is None:
             c = torch.empty(shp_c, dtype=cd, pin_memory=pin)
-        args = [_hptr(x, rd, "x"), _hptr(y, rd, "y"), _hptr(z, rd, "z") if self.dim == 3 else None,
+        args = [_hptr(x, rd, "x"), _hptr(y, rd, "y") if self.dim >= 2 else None,
+                _hptr(z, rd, "z") if self.dim == 3 else None,
                 _hptr(c, cd, "c"), _hptr(f, cd, "f")]
         _check(load().nufft_execute_host(self.handle, M, *args), "nufft_execute_host")
         self.M = M

@@ -123,7 +123,7 @@ int nufft_autotune(int type, int dim, const int64_t *nmodes, int iflag, int ntra
                    const void *z, void *c, void *f, int reps, nufft_opts *best, double *best_ms,
                    nufft_tune_trial *trials, int max_trials, int *ntrials)
 {
-    if (!best || reps < 1 || M < 1 || !c || !f) return NUFFT_ERR_ARG;
+    if (!best || reps < 1 || M < 1 || !c || !f || dim < 2) return NUFFT_ERR_ARG;   // 2D and 3D tiles
     nufft_opts o;
     nufft_default_opts(&o);
     if (base) o = *base;

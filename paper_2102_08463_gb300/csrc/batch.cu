@@ -81,9 +81,11 @@ cudaError_t multi_launch(const Group &g, const MultiLaunch &ml)
 {
     const bool t1 = g.type == 1;
     if (g.prec == 0) {
+        if (g.dim == 1) return t1 ? spread_multi_f32_1d(ml) : interp_multi_f32_1d(ml);
         if (g.dim == 2) return t1 ? spread_multi_f32_2d(ml) : interp_multi_f32_2d(ml);
         return t1 ? spread_multi_f32_3d(ml) : interp_multi_f32_3d(ml);
     }
+    if (g.dim == 1) return t1 ? spread_multi_f64_1d(ml) : interp_multi_f64_1d(ml);
     if (g.dim == 2) return t1 ? spread_multi_f64_2d(ml) : interp_multi_f64_2d(ml);
     return t1 ? spread_multi_f64_3d(ml) : interp_multi_f64_3d(ml);
 }

@@ -40,19 +40,23 @@ inline int default_bin_2d_type1(int axis, int prec, int w)
     if (axis == 0) return w <= 15 ? 16 - w : 32 - w;
     return prec == 0 ? 16 : 32;
 }
-// Default bin sizes of a plan (1 on unused axes): 16 x 16 (2D) and 16 x 16 x 2
-// (3D), with the row-sweep sizes above for 2D type 1 and, for 3D single-precision
-// type 1 at w <= 8, (16 - w) x 32 x 2: the padded width fills 16-lane sub-warps
-// and the taller bin halves the row flushes per point (29 x 8 x 128 bins on a
-// 256^3 grid, within the shared-memory counting sort).
+// Default bin sizes of a plan (1 on unused axes): 512 (1D), 16 x 16 (2D) and
+// 16 x 16 x 2 (3D), with the row-sweep sizes above for 2D type 1 and, for 3D single
+// precision at w <= 8 (both types), the plane-split sizes (16 - w) x 64 x 1
+// (w odd) or (16 - w) x 32 x 2 (w even): the padded width fills 16 lanes and
+// the padded depth m2 + w is even, so the two half-warps own equal plane sets;
+// the tall bins amortise the row flushes and loads (29 x 4 x 256 bins on a
+// 256^3 grid at w = 7, within the shared-memory counting sort).
 inline void default_bins(int type, int dim, int prec, int w, int out[3])
 {
     for (int d = 0; d < 3; ++d) out[d] = d < dim ? (dim == 2 ? 16 : (d < 2 ? 16 : 2)) : 1;
+    if (dim == 1) out[0] = 512;
     if (dim == 2 && type == 1)
         for (int d = 0; d < 2; ++d) out[d] = default_bin_2d_type1(d, prec, w);
-    if (dim == 3 && type == 1 && prec == 0 && w <= 8) {
+    if (dim == 3 && prec == 0 && w <= 8) {
         out[0] = 16 - w;
-        out[1] = 32;
+        out[1] = w % 2 ? 64 : 32;
+        out[2] = w % 2 ? 1 : 2;
     }
 }
 // Degree of the kernel polynomials of width w: the fits of the interior window
@@ -308,12 +312,16 @@ cudaError_t launch_binsort_into(const BinsortScratch &s, int prec, int dim, int6
 int64_t scan_parts_needed(int64_t L);
 int counting_sort_blocks(const Plan &p, int64_t M);
 int radix_sort_blocks(const Plan &p, int64_t M);
+cudaError_t spread_f32_1d(Plan &p, const void *c);
 cudaError_t spread_f32_2d(Plan &p, const void *c);
 cudaError_t spread_f32_3d(Plan &p, const void *c);
+cudaError_t spread_f64_1d(Plan &p, const void *c);
 cudaError_t spread_f64_2d(Plan &p, const void *c);
 cudaError_t spread_f64_3d(Plan &p, const void *c);
+cudaError_t interp_f32_1d(Plan &p, void *c);
 cudaError_t interp_f32_2d(Plan &p, void *c);
 cudaError_t interp_f32_3d(Plan &p, void *c);
+cudaError_t interp_f64_1d(Plan &p, void *c);
 cudaError_t interp_f64_2d(Plan &p, void *c);
 cudaError_t interp_f64_3d(Plan &p, void *c);
 
@@ -332,10 +340,15 @@ struct MultiLaunch {
     int tile;                  // largest padded bin (cells) over the plans
     cudaStream_t stream;
 };
-// Row-sweep form of a type 1 SM plan (the batch's grouping key): 2D sub-warp
-// lanes 8, 16 or 32; 3D: bin depth m2 (1 or 2), plus 4 for 16-lane sub-warps;
-// 0 if the plan uses the shared-memory atomic kernel.
+// Row-sweep form of an SM plan (the batch's grouping key).  Type 1: 2D sub-warp
+// lanes 8, 16 or 32; 3D: bin depth m2 (1 or 2), plus 4 for the plane-split form
+// (padded width <= 16).  Type 2: m2 + 4 for the 3D plane-split interpolation.
+// 0 if the plan uses the shared-memory kernels.
 int sweep_variant(const Plan &p);
+cudaError_t spread_multi_f32_1d(const MultiLaunch &ml);
+cudaError_t spread_multi_f64_1d(const MultiLaunch &ml);
+cudaError_t interp_multi_f32_1d(const MultiLaunch &ml);
+cudaError_t interp_multi_f64_1d(const MultiLaunch &ml);
 cudaError_t spread_multi_f32_2d(const MultiLaunch &ml);
 cudaError_t spread_multi_f32_3d(const MultiLaunch &ml);
 cudaError_t spread_multi_f64_2d(const MultiLaunch &ml);

@@ -282,8 +282,11 @@ void nufft::fit_kernel_poly(Plan &p)
 
 int nufft::sweep_variant(const Plan &p)
 {
-    if (p.type != 1 || p.method != NUFFT_METHOD_SM) return 0;
+    if (p.method != NUFFT_METHOD_SM) return 0;
     const int p0 = padded(p.m[0], p.w);
+    if (p.type == 2)   // the plane-split interpolation sweep (3D single, p0 <= 16)
+        return p.dim == 3 && p.prec == 0 && p.w <= 8 && p0 <= 16 && (p.m[2] == 1 || p.m[2] == 2)
+                   ? p.m[2] + 4 : 0;
     if (p0 > 32) return 0;
     if (p.dim == 2) return p0 <= 8 ? 8 : (p0 <= 16 ? 16 : 32);
     if (p.prec == 0 && p.w <= 8 && (p.m[2] == 1 || p.m[2] == 2)) return p.m[2] + (p0 <= 16 ? 4 : 0);
@@ -375,7 +378,7 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
 {
     if (!out) return NUFFT_ERR_ARG;
     *out = nullptr;
-    if ((type != 1 && type != 2) || (dim != 2 && dim != 3) || !nmodes) return NUFFT_ERR_ARG;
+    if ((type != 1 && type != 2) || dim < 1 || dim > 3 || !nmodes) return NUFFT_ERR_ARG;
     if (iflag != 1 && iflag != -1) return NUFFT_ERR_ARG;
     if (ntransf < 1 || prec < -1 || prec > 1) return NUFFT_ERR_ARG;
     if (!(eps > 0.0) || !isfinite(eps)) return NUFFT_ERR_EPS;
@@ -458,8 +461,9 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     if (p.nbins > ((int64_t)1 << 30)) { delete h; return NUFFT_ERR_SIZE; }
 
     p.method = o.method == NUFFT_METHOD_AUTO ? default_method(p, (size_t)smem_optin) : o.method;
+    // measured / learned tiles (autotuner, picker) cover 2D and 3D
     p.auto_tiles = o.method == NUFFT_METHOD_AUTO && o.bin[0] == 0 && o.bin[1] == 0 &&
-                   o.bin[2] == 0 && o.msub == 0 && o.threads == 0;
+                   o.bin[2] == 0 && o.msub == 0 && o.threads == 0 && dim >= 2;
     p.use_picker = p.auto_tiles && o.use_picker != 0;
     p.unordered_bins = o.unordered_bins != 0;
     p.debug_checks = o.debug_checks != 0;
@@ -557,7 +561,7 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
     if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
     if (M < 0 || M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_ARG;
-    if (M > 0 && (!x || !y || (p.dim == 3 && !z))) return NUFFT_ERR_ARG;
+    if (M > 0 && (!x || (p.dim >= 2 && !y) || (p.dim == 3 && !z))) return NUFFT_ERR_ARG;
     p.have_pts = false;
     if (p.auto_tiles) {
         // measured tiles from the autotuner's cache first, then the picker's
@@ -669,8 +673,10 @@ int nufft_spread_add(nufft_plan h, const void *c)
     cudaError_t e;
     int method = p.method;
     if (p.type == 2 && method == NUFFT_METHOD_SM) p.method = NUFFT_METHOD_GM_SORT;   // SM spread needs its smem
-    if (p.prec == 0) e = p.dim == 2 ? spread_f32_2d(p, c) : spread_f32_3d(p, c);
-    else e = p.dim == 2 ? spread_f64_2d(p, c) : spread_f64_3d(p, c);
+    if (p.prec == 0)
+        e = p.dim == 1 ? spread_f32_1d(p, c) : p.dim == 2 ? spread_f32_2d(p, c) : spread_f32_3d(p, c);
+    else
+        e = p.dim == 1 ? spread_f64_1d(p, c) : p.dim == 2 ? spread_f64_2d(p, c) : spread_f64_3d(p, c);
     p.method = method;
     return cuda_err(e);
 }
@@ -683,8 +689,10 @@ int nufft_interp(nufft_plan h, void *c)
     if (p.M == 0) return NUFFT_OK;
     if (!c) return NUFFT_ERR_ARG;
     cudaError_t e;
-    if (p.prec == 0) e = p.dim == 2 ? interp_f32_2d(p, c) : interp_f32_3d(p, c);
-    else e = p.dim == 2 ? interp_f64_2d(p, c) : interp_f64_3d(p, c);
+    if (p.prec == 0)
+        e = p.dim == 1 ? interp_f32_1d(p, c) : p.dim == 2 ? interp_f32_2d(p, c) : interp_f32_3d(p, c);
+    else
+        e = p.dim == 1 ? interp_f64_1d(p, c) : p.dim == 2 ? interp_f64_2d(p, c) : interp_f64_3d(p, c);
     return cuda_err(e);
 }
 
@@ -738,7 +746,7 @@ int nufft_execute_host(nufft_plan h, int64_t M, const void *x, const void *y, co
     if (!h || !f) return NUFFT_ERR_ARG;
     Plan &p = h->p;
     if (M < 0 || M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_ARG;
-    if (M > 0 && (!x || !y || (p.dim == 3 && !z) || !c)) return NUFFT_ERR_ARG;
+    if (M > 0 && (!x || (p.dim >= 2 && !y) || (p.dim == 3 && !z) || !c)) return NUFFT_ERR_ARG;
     const size_t rs = real_size(p), cs = 2 * rs;
     int rc = NUFFT_OK;
     // staging and the copy stream, made once and grown with M
@@ -783,7 +791,8 @@ int nufft_execute_host(nufft_plan h, int64_t M, const void *x, const void *y, co
     }
     if (e == cudaSuccess) e = cudaEventRecord(p.hx_ev[1], p.hx_copy);
     if (e != cudaSuccess) return cuda_err(e);
-    rc = nufft_setpts(h, M, p.hx_pts[0], p.hx_pts[1], p.dim == 3 ? p.hx_pts[2] : nullptr);
+    rc = nufft_setpts(h, M, p.hx_pts[0], p.dim >= 2 ? p.hx_pts[1] : nullptr,
+                      p.dim == 3 ? p.hx_pts[2] : nullptr);
     if (rc != NUFFT_OK) return rc;
     e = cudaStreamWaitEvent(st, p.hx_ev[1], 0);
     if (e != cudaSuccess) return cuda_err(e);

@@ -136,7 +136,7 @@ template <typename T, int DIM>
 __device__ __forceinline__ int bin_of_v(T xv, T yv, T zv, int3 n, int3 m, int3 nb)
 {
     int lx = (int)__umul64hi(period_fraction(xv), (uint64_t)n.x);
-    int ly = (int)__umul64hi(period_fraction(yv), (uint64_t)n.y);
+    int ly = DIM >= 2 ? (int)__umul64hi(period_fraction(yv), (uint64_t)n.y) : 0;
     int bz = 0;
     if (DIM == 3) bz = (int)__umul64hi(period_fraction(zv), (uint64_t)n.z) / m.z;
     return lx / m.x + nb.x * (ly / m.y + nb.y * bz);
@@ -146,7 +146,7 @@ template <typename T, int DIM>
 __device__ __forceinline__ int bin_of(const T *x, const T *y, const T *z, int64_t j, int3 n,
                                       int3 m, int3 nb)
 {
-    return bin_of_v<T, DIM>(x[j], y[j], DIM == 3 ? z[j] : (T)0, n, m, nb);
+    return bin_of_v<T, DIM>(x[j], DIM >= 2 ? y[j] : (T)0, DIM == 3 ? z[j] : (T)0, n, m, nb);
 }
 
 template <typename T> __device__ __forceinline__ uint32_t unpack_word_t(T v);
@@ -171,11 +171,15 @@ __device__ __forceinline__ typename rec4<T>::type make_record_v(T xv, T yv, T zv
 {
     const int P = pad_lo(w);
     AxisPos<T> px = axis_position<T>(period_fraction(xv), n.x, w);
-    AxisPos<T> py = axis_position<T>(period_fraction(yv), n.y, w);
     uint32_t sx = (uint32_t)(px.l0 - ((px.l / m.x) * m.x - P));
-    uint32_t sy = (uint32_t)(py.l0 - ((py.l / m.y) * m.y - P));
+    uint32_t sy = 0;
+    T dy = 0, dz = 0;
+    if (DIM >= 2) {
+        AxisPos<T> py = axis_position<T>(period_fraction(yv), n.y, w);
+        sy = (uint32_t)(py.l0 - ((py.l / m.y) * m.y - P));
+        dy = py.delta;
+    }
     uint32_t sz = 0;
-    T dz = 0;
     if (DIM == 3) {
         AxisPos<T> pz = axis_position<T>(period_fraction(zv), n.z, w);
         sz = (uint32_t)(pz.l0 - ((pz.l / m.z) * m.z - P));
@@ -183,7 +187,7 @@ __device__ __forceinline__ typename rec4<T>::type make_record_v(T xv, T yv, T zv
     }
     typename rec4<T>::type r;
     r.x = px.delta;
-    r.y = py.delta;
+    r.y = dy;
     r.z = dz;
     r.w = packed_word<T>(sx | (sy << 10) | (sz << 20));
     return r;
@@ -219,7 +223,7 @@ count_kernel(const T *__restrict__ x, const T *__restrict__ y, const T *__restri
             xv[k] = yv[k] = zv[k] = (T)0;
             if (j < end) {
                 xv[k] = x[j];
-                yv[k] = y[j];
+                if (DIM >= 2) yv[k] = y[j];
                 if (DIM == 3) zv[k] = z[j];
                 key[k] = 0;
             }
@@ -449,8 +453,8 @@ records_from_perm_kernel(const int32_t *__restrict__ perm, int64_t M, const T *_
          i += (int64_t)gridDim.x * blockDim.x) {
         const int j = perm[i];
         typename rec4<T>::type r =
-            make_record_v<T, DIM>(x[j], y[j], DIM == 3 ? z[j] : (T)0, n, m, w);
-        if (DIM == 2) r.z = packed_word<T>((uint32_t)j);
+            make_record_v<T, DIM>(x[j], DIM >= 2 ? y[j] : (T)0, DIM == 3 ? z[j] : (T)0, n, m, w);
+        if (DIM != 3) r.z = packed_word<T>((uint32_t)j);
         recs[i] = r;
     }
 }
@@ -465,7 +469,7 @@ __global__ void keys_kernel(const T *__restrict__ x, const T *__restrict__ y,
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const T xv = x[j], yv = y[j], zv = DIM == 3 ? z[j] : (T)0;
+        const T xv = x[j], yv = DIM >= 2 ? y[j] : (T)0, zv = DIM == 3 ? z[j] : (T)0;
         keys[j] = bin_of_v<T, DIM>(xv, yv, zv, n, m, nb);
     }
 }
@@ -596,7 +600,7 @@ __global__ void check_coords_kernel(const T *__restrict__ x, const T *__restrict
     bool bad = false;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M;
          j += (int64_t)gridDim.x * blockDim.x) {
-        bad |= !(x[j] >= -lim && x[j] <= lim) || !(y[j] >= -lim && y[j] <= lim) ||
+        bad |= !(x[j] >= -lim && x[j] <= lim) || (y != nullptr && !(y[j] >= -lim && y[j] <= lim)) ||
                (z != nullptr && !(z[j] >= -lim && z[j] <= lim));
     }
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1);
@@ -624,11 +628,13 @@ cudaError_t launch_checks(Plan &p, const void *x, const void *y, const void *z)
     count_launch(2);
     if (p.prec == 0)
         check_coords_kernel<float><<<g, 256, 0, p.stream>>>(
-            (const float *)x, (const float *)y, p.dim == 3 ? (const float *)z : nullptr, p.M,
+            (const float *)x, p.dim >= 2 ? (const float *)y : nullptr,
+            p.dim == 3 ? (const float *)z : nullptr, p.M,
             p.dstatus);
     else
         check_coords_kernel<double><<<g, 256, 0, p.stream>>>(
-            (const double *)x, (const double *)y, p.dim == 3 ? (const double *)z : nullptr, p.M,
+            (const double *)x, p.dim >= 2 ? (const double *)y : nullptr,
+            p.dim == 3 ? (const double *)z : nullptr, p.M,
             p.dstatus);
     if (p.method == NUFFT_METHOD_GM) return cudaGetLastError();   // GM sorts nothing
     cudaError_t e = cudaMemsetAsync(p.keys_alt, 0, sizeof(int32_t) * p.M, p.stream);
@@ -692,12 +698,9 @@ cudaError_t launch_records(Plan &p, const T *x, const T *y, const T *z,
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     count_launch();
-    if (p.dim == 2)
-        records_from_perm_kernel<T, 2><<<(unsigned)g, 256, 0, p.stream>>>(p.perm, p.M, x, y, z, n,
-                                                                         m, p.w, recs);
-    else
-        records_from_perm_kernel<T, 3><<<(unsigned)g, 256, 0, p.stream>>>(p.perm, p.M, x, y, z, n,
-                                                                         m, p.w, recs);
+    auto k = p.dim == 1 ? records_from_perm_kernel<T, 1>
+             : p.dim == 2 ? records_from_perm_kernel<T, 2> : records_from_perm_kernel<T, 3>;
+    k<<<(unsigned)g, 256, 0, p.stream>>>(p.perm, p.M, x, y, z, n, m, p.w, recs);
     return cudaGetLastError();
 }
 
@@ -721,7 +724,7 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
     if (cblk > 0) {
         const int64_t chunk = (M + cblk - 1) / cblk;
         const size_t smem = (size_t)nbins * sizeof(int32_t);
-        auto kc = p.dim == 2 ? count_kernel<T, 2> : count_kernel<T, 3>;
+        auto kc = p.dim == 1 ? count_kernel<T, 1> : p.dim == 2 ? count_kernel<T, 2> : count_kernel<T, 3>;
         auto ks = p.unordered_bins ? rank_scatter_kernel<false> : rank_scatter_kernel<true>;
         e = allow_max_smem((const void *)kc);
         if (e == cudaSuccess) e = allow_max_smem((const void *)ks);
@@ -741,10 +744,8 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
     } else {
         const int g = grid_for(M, 256, p.num_sms);
         count_launch();
-        if (p.dim == 2)
-            keys_kernel<T, 2><<<g, 256, 0, st>>>(x, y, z, M, n, m, nb, p.keys);
-        else
-            keys_kernel<T, 3><<<g, 256, 0, st>>>(x, y, z, M, n, m, nb, p.keys);
+        auto kk = p.dim == 1 ? keys_kernel<T, 1> : p.dim == 2 ? keys_kernel<T, 2> : keys_kernel<T, 3>;
+        kk<<<g, 256, 0, st>>>(x, y, z, M, n, m, nb, p.keys);
         e = cudaMemsetAsync(p.bincount, 0, sizeof(int32_t) * p.nbins, st);
         if (e != cudaSuccess) return e;
         count_launch();

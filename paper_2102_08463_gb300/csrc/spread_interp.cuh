@@ -843,15 +843,193 @@ __device__ __forceinline__ void spread_sweep3_sub(const KArgs<T> &a, int4 sub, i
     for (int j = 0; j < W; ++j) flush_row(row + j, acc[j]);
 }
 
+// ---------------------------------------------------------------------------
+// Plane-split row sweep, 3D (single precision, padded width p0 <= 16, W <= 8).
+// The warp is two halves of 16 lanes; lane (h, q) owns x column q of the padded
+// bin and the KZ = (M2 + W + 1) / 2 planes h KZ .. h KZ + KZ - 1, each with its
+// W window rows in registers (slot s = padded row mod W, as in 2D).  Every lane
+// takes part in every point: the point's c w_x row (zero outside the window)
+// and its z weights (zero outside the window) are staged, so the update
+//   acc[i][s] += (c w_x[q] w_z[h KZ + i]) w_y[s],  i < KZ, s < W
+// has no branch on the point's start plane.  The two halves hold different
+// planes, so a finished row goes to the fine grid without any reduction: each
+// lane adds its KZ cells of that row.  Points are ordered by window start row
+// only (Sec. 4.1 SM step 2 with the subproblem's accumulators in registers).
+template <int W, int M2> __host__ __device__ constexpr int planes3_kz() { return (M2 + W + 1) / 2; }
+// slot: W rotated w_y dup pairs, 2 KZ w_z dup pairs, the 16-wide c w_x row
+template <int W, int M2> __host__ __device__ constexpr int planes3_owz() { return 4 * ((W + 1) / 2); }
+template <int W, int M2> __host__ __device__ constexpr int planes3_ocx()
+{
+    return planes3_owz<W, M2>() + 4 * planes3_kz<W, M2>();
+}
+template <int W, int M2> __host__ __device__ constexpr int planes3_slot()
+{
+    return ((planes3_ocx<W, M2>() + 32) / 4 | 1) * 4;
+}
+template <int W, int M2>
+__host__ __device__ inline size_t planes3_bytes(int m1)
+{
+    return sweep_head(m1 + 1) + sizeof(float) * (size_t)32 * planes3_slot<W, M2>();
+}
+
+template <typename T, int W, int M2>
+__device__ __forceinline__ void spread_planes3_sub(const KArgs<T> &a, int4 sub, int tr,
+                                                   unsigned char *sm)
+{
+    static_assert(sizeof(T) == 4, "the 3D row sweep is single precision");
+    using C = float2;
+    using R = typename rec4<T>::type;
+    constexpr int KZ = planes3_kz<W, M2>();
+    constexpr int PZ = M2 + W;
+    constexpr int SLOT = planes3_slot<W, M2>();
+    constexpr int OWZ = planes3_owz<W, M2>(), OCX = planes3_ocx<W, M2>();
+    const int lane = threadIdx.x & 31, h = lane >> 4, q = lane & 15;
+    const int n = sub.z;
+    uint16_t *idx = reinterpret_cast<uint16_t *>(sm);
+    int *cnt = reinterpret_cast<int *>(sm + 2 * kSweepCap);
+    float *stg = reinterpret_cast<float *>(sm + sweep_head(a.m1 + 1));
+    int o0, o1, o2;
+    bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
+    const int P = pad_lo(W);
+    const C *cin = a.cin + (int64_t)tr * a.M;
+    C *grid = a.grid + (int64_t)tr * a.nftot;
+    const bool xok = q < a.p0;
+    const int gx = wrap_any(o0 - P + (xok ? q : 0), a.n0);
+    const int grow0 = wrap_any(o1 - P, a.n1);
+    int gz[KZ];                                            // fine-grid plane of each owned plane
+#pragma unroll
+    for (int i = 0; i < KZ; ++i) gz[i] = wrap_any(o2 - P + h * KZ + i, a.n2);
+    float2 acc[KZ][W];
+#pragma unroll
+    for (int i = 0; i < KZ; ++i)
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[i][k] = make_float2(0.f, 0.f);
+    // add window slot k of every owned plane to fine-grid row g and clear it
+    auto flush = [&](int k, int g) {
+#pragma unroll
+        for (int i = 0; i < KZ; ++i) {
+            const float2 v = acc[i][k < W ? k : 0];
+            acc[i][k < W ? k : 0] = make_float2(0.f, 0.f);
+            if (xok && h * KZ + i < PZ && (v.x != 0.f || v.y != 0.f))
+                atomic_add_cplx(&grid[((int64_t)gz[i] * a.n1 + g) * a.n0 + gx], v.x, v.y);
+        }
+    };
+    auto step = [&](int i) {
+        const float *s = stg + i * SLOT;
+        const float2 cx = *reinterpret_cast<const float2 *>(s + OCX + 2 * q);
+        float2 t[KZ];
+        if constexpr (KZ % 2 == 0) {
+#pragma unroll
+            for (int j = 0; j < KZ; j += 2) {
+                const float4 z2 = *reinterpret_cast<const float4 *>(s + OWZ + 2 * (h * KZ + j));
+                t[j] = mul2(cx, make_float2(z2.x, z2.y));
+                t[j + 1] = mul2(cx, make_float2(z2.z, z2.w));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < KZ; ++j)
+                t[j] = mul2(cx, *reinterpret_cast<const float2 *>(s + OWZ + 2 * (h * KZ + j)));
+        }
+#pragma unroll
+        for (int k = 0; k < W; k += 2) {
+            const float4 wp = *reinterpret_cast<const float4 *>(s + 2 * k);
+#pragma unroll
+            for (int j = 0; j < KZ; ++j) {
+                fma2(acc[j][k], t[j], make_float2(wp.x, wp.y));
+                if (k + 1 < W) fma2(acc[j][k + 1 < W ? k + 1 : k], t[j], make_float2(wp.z, wp.w));
+            }
+        }
+    };
+
+    const R *recs = a.recs + sub.y;
+    for (int piece = 0; piece < n; piece += kSweepCap) {
+        const int np = min(kSweepCap, n - piece);
+        sweep_row_order<T, 0>(recs + piece, np, a.m1 + 1, idx, cnt);
+        R rc;
+        C cv;
+        if (lane < np) {
+            rc = recs[piece + idx[lane]];
+            cv = cin[a.order[sub.y + piece + idx[lane]]];
+        }
+        int bbase = -32, bend = 0;                         // staged positions [bbase, bend)
+        auto stage_next = [&]() {
+            __syncwarp();                                  // the old slots are consumed
+            bbase += 32;
+            const int c = min(32, np - bbase);
+            if (lane < c) {
+                const uint32_t pk = unpack_word<T>(rc.w);
+                float *s = stg + lane * SLOT;
+                const int sx = (int)(pk & 1023u);
+                const int sy = (int)((pk >> 10) & 1023u);
+                const int sz = (int)(pk >> 20);
+                float vx[W], vy[W], vz[W];
+                kernel_row<T, W>(a, rc.x, vx);
+                kernel_row<T, W>(a, rc.y, vy);
+                kernel_row<T, W>(a, rc.z, vz);
+#pragma unroll
+                for (int k = 0; k < 32; k += 4) store_zero_quad(s + OCX + k);
+#pragma unroll
+                for (int k = 0; k < 4 * KZ; k += 4) store_zero_quad(s + OWZ + k);
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) =
+                        make_float2(cv.x * vx[i], cv.y * vx[i]);
+                    *reinterpret_cast<float2 *>(s + OWZ + 2 * (sz + i)) = make_float2(vz[i], vz[i]);
+                }
+                int slot = sy % W;                         // w_y[k] goes to slot (sy + k) mod W
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    *reinterpret_cast<float2 *>(s + 2 * slot) = make_float2(vy[k], vy[k]);
+                    slot = slot + 1 == W ? 0 : slot + 1;
+                }
+            }
+            const int nb = bbase + 32;                     // prefetch the next batch
+            if (nb + lane < np) {
+                rc = recs[piece + idx[nb + lane]];
+                cv = cin[a.order[sub.y + piece + idx[nb + lane]]];
+            }
+            bend = bbase + c;
+            __syncwarp();
+        };
+        int pos = 0;
+        int g = grow0;
+        int k = 0;                                         // slot of row r = r mod W
+#pragma unroll 1
+        for (int r = 0; r < a.p1; ++r) {
+            const int end = r <= a.m1 ? cnt[r] : pos;
+            while (pos < end) {
+                if (pos == bend) stage_next();
+                const int e = min(end, bend);
+                const int ie = e - bbase;
+#pragma unroll 1
+                for (int i = pos - bbase; i < ie; ++i) step(i);
+                pos = e;
+            }
+#pragma unroll
+            for (int kk = 0; kk < W; ++kk)                 // row r is complete: flush slot k
+                if (kk == k) flush(kk, g);
+            g = g + 1 == a.n1 ? 0 : g + 1;
+            k = k + 1 == W ? 0 : k + 1;
+        }
+        __syncwarp();                                      // idx / cnt reused by the next piece
+    }
+}
+
 template <typename T, int W, int M2, int L>
 __device__ __forceinline__ void spread_sweep3_item(const KArgs<T> &a, int sp, int tr,
                                                    unsigned char *sm)
 {
-    spread_sweep3_sub<T, W, M2, L>(a, a.subprob[sp], tr, sm);
+    if constexpr (L == 16)
+        spread_planes3_sub<T, W, M2>(a, a.subprob[sp], tr, sm);
+    else
+        spread_sweep3_sub<T, W, M2, L>(a, a.subprob[sp], tr, sm);
 }
 
+// Four warps per CTA; the plane-split form (L = 16) fits three CTAs per SM.
+template <int L> __host__ __device__ constexpr int sweep3_threads() { return 128; }
+
 template <typename T, int W, int M2, int L>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(sweep3_threads<L>(), L == 16 ? 3 : 1)
 spread_sweep3_kernel(KArgs<T> a, int warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1147,6 +1325,233 @@ __device__ __forceinline__ void interp_lane_item(const KArgs<T> &a, int sp, int 
         cout[j] = o;
     }
     if (STAGED) __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Plane-split row sweep for 3D interpolation (single precision, p0 <= 16,
+// W <= 8; Sec. 4.2 with the padded bin held in registers instead of shared
+// memory).  Lane (h, q) owns x column q and planes h KZ .. h KZ + KZ - 1 of
+// the padded bin, as in the spreading sweep, and holds the W padded rows that
+// a window starting at the current row reads (slot = row mod W), loaded from
+// the fine grid one row ahead of their first use.  The points, ordered by
+// window start row, are staged 32 at a time (w_x as a 16-wide row, w_z as a
+// PZ-wide row, both zero outside the window; w_y rotated to the row slots);
+// for each point every lane forms
+//   sum_i (w_x[q] w_z[h KZ + i]) sum_s g[i][s] w_y[s]
+// and a butterfly sum over the warp gives the point's value, kept by the lane
+// that staged it and stored once per batch.
+template <int W, int M2> __host__ __device__ constexpr int iplanes3_owz() { return 4 * ((W + 1) / 2); }
+template <int W, int M2> __host__ __device__ constexpr int iplanes3_owx()
+{
+    return iplanes3_owz<W, M2>() + 4 * ((2 * planes3_kz<W, M2>() + 3) / 4);
+}
+template <int W, int M2> __host__ __device__ constexpr int iplanes3_slot()
+{
+    return ((iplanes3_owx<W, M2>() + 16) / 4 | 1) * 4;
+}
+template <int W, int M2>
+__host__ __device__ inline size_t iplanes3_bytes(int m1)
+{
+    return sweep_head(m1 + 1) + sizeof(float) * (size_t)32 * iplanes3_slot<W, M2>();
+}
+
+template <typename T, int W, int M2>
+__device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, int tr,
+                                                   unsigned char *sm)
+{
+    static_assert(sizeof(T) == 4, "the 3D row sweep is single precision");
+    using C = float2;
+    using R = typename rec4<T>::type;
+    constexpr int KZ = planes3_kz<W, M2>();
+    constexpr int PZ = M2 + W;
+    constexpr int SLOT = iplanes3_slot<W, M2>();
+    constexpr int OWZ = iplanes3_owz<W, M2>(), OWX = iplanes3_owx<W, M2>();
+    const int lane = threadIdx.x & 31, h = lane >> 4, q = lane & 15;
+    const int n = sub.z;
+    uint16_t *idx = reinterpret_cast<uint16_t *>(sm);
+    int *cnt = reinterpret_cast<int *>(sm + 2 * kSweepCap);
+    float *stg = reinterpret_cast<float *>(sm + sweep_head(a.m1 + 1));
+    int o0, o1, o2;
+    bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
+    const int P = pad_lo(W);
+    const C *grid = a.grid + (int64_t)tr * a.nftot;
+    C *cout = a.cout + (int64_t)tr * a.M;
+    const bool xok = q < a.p0;
+    const int gx = wrap_any(o0 - P + (xok ? q : 0), a.n0);
+    const int grow0 = wrap_any(o1 - P, a.n1);
+    const C *col[KZ];                                      // (plane, column) of each owned cell
+    bool cok[KZ];
+#pragma unroll
+    for (int i = 0; i < KZ; ++i) {
+        cok[i] = xok && h * KZ + i < PZ;
+        col[i] = grid + (int64_t)wrap_any(o2 - P + h * KZ + i, a.n2) * a.n1 * a.n0 + gx;
+    }
+    auto load_row = [&](int g, float2 (&dst)[KZ]) {
+#pragma unroll
+        for (int i = 0; i < KZ; ++i)
+            dst[i] = cok[i] ? __ldg(col[i] + (int64_t)g * a.n0) : make_float2(0.f, 0.f);
+    };
+    float2 g[KZ][W];                                       // g[i][slot]
+    float2 nxt[KZ];
+
+    const R *recs = a.recs + sub.y;
+    for (int piece = 0; piece < n; piece += kSweepCap) {
+        const int np = min(kSweepCap, n - piece);
+        sweep_row_order<T, 0>(recs + piece, np, a.m1 + 1, idx, cnt);
+        // rows 0 .. W-1 into their slots, row W in flight
+        {
+            int gy = grow0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                float2 v[KZ];
+                load_row(gy, v);
+#pragma unroll
+                for (int i = 0; i < KZ; ++i) g[i][k] = v[i];
+                gy = gy + 1 == a.n1 ? 0 : gy + 1;
+            }
+            load_row(gy, nxt);
+        }
+        R rc;
+        int jn = 0;
+        if (lane < np) {
+            rc = recs[piece + idx[lane]];
+            jn = a.order[sub.y + piece + idx[lane]];
+        }
+        int bbase = -32, bend = 0, jout = 0;
+        float2 res = make_float2(0.f, 0.f);
+        auto stage_next = [&]() {
+            __syncwarp();
+            if (bbase >= 0 && bbase + lane < bend) cout[jout] = res;   // the finished batch
+            bbase += 32;
+            const int c = min(32, np - bbase);
+            if (lane < c) {
+                const uint32_t pk = unpack_word<T>(rc.w);
+                float *s = stg + lane * SLOT;
+                const int sx = (int)(pk & 1023u);
+                const int sy = (int)((pk >> 10) & 1023u);
+                const int sz = (int)(pk >> 20);
+                float vx[W], vy[W], vz[W];
+                kernel_row<T, W>(a, rc.x, vx);
+                kernel_row<T, W>(a, rc.y, vy);
+                kernel_row<T, W>(a, rc.z, vz);
+#pragma unroll
+                for (int k = 0; k < 16; k += 4) store_zero_quad(s + OWX + k);
+#pragma unroll
+                for (int k = 0; k < OWX - OWZ; k += 4) store_zero_quad(s + OWZ + k);
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    s[OWX + sx + i] = vx[i];
+                    s[OWZ + sz + i] = vz[i];
+                }
+                int slot = sy % W;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    *reinterpret_cast<float2 *>(s + 2 * slot) = make_float2(vy[k], vy[k]);
+                    slot = slot + 1 == W ? 0 : slot + 1;
+                }
+                jout = jn;
+            }
+            const int nb = bbase + 32;
+            if (nb + lane < np) {
+                rc = recs[piece + idx[nb + lane]];
+                jn = a.order[sub.y + piece + idx[nb + lane]];
+            }
+            bend = bbase + c;
+            __syncwarp();
+        };
+        auto step = [&](int i) {
+            const float *s = stg + i * SLOT;
+            const float wx = s[OWX + q];
+            float wz[KZ];
+            if constexpr (KZ % 4 == 0) {
+#pragma unroll
+                for (int j = 0; j < KZ; j += 4) {
+                    const float4 z4 = *reinterpret_cast<const float4 *>(s + OWZ + h * KZ + j);
+                    wz[j] = z4.x;
+                    wz[j + 1] = z4.y;
+                    wz[j + 2] = z4.z;
+                    wz[j + 3] = z4.w;
+                }
+            } else if constexpr (KZ % 2 == 0) {
+#pragma unroll
+                for (int j = 0; j < KZ; j += 2) {
+                    const float2 z2 = *reinterpret_cast<const float2 *>(s + OWZ + h * KZ + j);
+                    wz[j] = z2.x;
+                    wz[j + 1 < KZ ? j + 1 : j] = z2.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < KZ; ++j) wz[j] = s[OWZ + h * KZ + j];
+            }
+            float2 u[KZ];
+#pragma unroll
+            for (int k = 0; k < W; k += 2) {
+                const float4 wp = *reinterpret_cast<const float4 *>(s + 2 * k);
+#pragma unroll
+                for (int j = 0; j < KZ; ++j) {
+                    if (k == 0) u[j] = mul2(g[j][0], make_float2(wp.x, wp.y));
+                    else fma2(u[j], g[j][k], make_float2(wp.x, wp.y));
+                    if (k + 1 < W) fma2(u[j], g[j][k + 1 < W ? k + 1 : k], make_float2(wp.z, wp.w));
+                }
+            }
+            float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < KZ; ++j) {
+                const float t = wx * wz[j];
+                fma2(v, u[j], make_float2(t, t));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v = __fadd2_rn(v, make_float2(__shfl_xor_sync(kFullMask, v.x, o),
+                                              __shfl_xor_sync(kFullMask, v.y, o)));
+            if (lane == i) res = v;
+        };
+        int pos = 0;
+        int gy = grow0 + W < a.n1 ? grow0 + W : (grow0 + W) % a.n1;   // row of nxt
+        int k = 0;                                         // slot of row r
+#pragma unroll 1
+        for (int r = 0; r <= a.m1; ++r) {
+            const int end = cnt[r];
+            while (pos < end) {
+                if (pos == bend) stage_next();
+                const int e = min(end, bend);
+                const int ie = e - bbase;
+#pragma unroll 1
+                for (int i = pos - bbase; i < ie; ++i) step(i);
+                pos = e;
+            }
+            // row r is no longer read: its slot takes row r + W, the next row loads
+#pragma unroll
+            for (int kk = 0; kk < W; ++kk)
+                if (kk == k) {
+#pragma unroll
+                    for (int i = 0; i < KZ; ++i) g[i][kk] = nxt[i];
+                }
+            gy = gy + 1 == a.n1 ? 0 : gy + 1;
+            if (r + W + 1 < a.p1) load_row(gy, nxt);
+            k = k + 1 == W ? 0 : k + 1;
+        }
+        __syncwarp();
+        if (bbase >= 0 && bbase + lane < bend) cout[jout] = res;
+        __syncwarp();                                      // idx / cnt reused by the next piece
+    }
+}
+
+template <typename T, int W, int M2>
+__global__ void __launch_bounds__(128, 3)
+interp_planes3_kernel(KArgs<T> a, int warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char *sm = smem_raw + (size_t)warp * warp_bytes;
+    const int per_cta = blockDim.x >> 5;
+    const int nsp = *a.nsub;
+    const int64_t nwork = (int64_t)nsp * a.ntransf;
+    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
+         wi += (int64_t)gridDim.x * per_cta) {
+        const int sp = (int)(wi % nsp);
+        interp_planes3_sub<T, W, M2>(a, a.subprob[sp], (int)(wi / nsp), sm);
+    }
 }
 
 // Asynchronous global -> shared copies (cp.async, sm_80+): the data land in
@@ -1445,8 +1850,32 @@ spread_sweep2_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__r
     }
 }
 
+template <typename T, int W, int M2>
+__global__ void __launch_bounds__(128, 3)
+interp_planes3_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
+                            int nplans, int warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char *base = smem_raw + (size_t)warp * (args_slot<T>() + warp_bytes);
+    KArgs<T> *cache = reinterpret_cast<KArgs<T> *>(base);
+    unsigned char *sm = base + args_slot<T>();
+    const int per_cta = blockDim.x >> 5;
+    int cached = -1;
+    const int64_t nwork = workoff[nplans];
+    for (int64_t wi = (int64_t)blockIdx.x * per_cta + warp; wi < nwork;
+         wi += (int64_t)gridDim.x * per_cta) {
+        const int pl = batch_plan_of(workoff, nplans, wi);
+        warp_load_args(args, pl, cache, cached);
+        const KArgs<T> &a = *cache;
+        const int64_t local = wi - workoff[pl];
+        const int nsp = *a.nsub;
+        interp_planes3_sub<T, W, M2>(a, a.subprob[(int)(local % nsp)], (int)(local / nsp), sm);
+    }
+}
+
 template <typename T, int W, int M2, int L>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(sweep3_threads<L>(), L == 16 ? 3 : 1)
 spread_sweep3_multi_kernel(const KArgs<T> *__restrict__ args, const int64_t *__restrict__ workoff,
                            int nplans, int warp_bytes)
 {
@@ -1636,12 +2065,32 @@ bool launch_sweep2(Plan &p, const KArgs<T> &a, int threads, cudaError_t *err)
 template <typename T, int W, int M2, int L>
 bool launch_sweep3(Plan &p, const KArgs<T> &a, cudaError_t *err)
 {
-    const size_t warp_bytes = sweep3_bytes<T, W, M2, L>(a.m1);
-    int nw = 4;
+    size_t warp_bytes;
+    if constexpr (L == 16) warp_bytes = planes3_bytes<W, M2>(a.m1);
+    else warp_bytes = sweep3_bytes<T, W, M2, L>(a.m1);
+    int nw = sweep3_threads<L>() / 32;
     while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
     if (nw < 2) return false;
     const size_t smem = warp_bytes * nw;
     auto k = spread_sweep3_kernel<T, W, M2, L>;
+    if (cudaError_t ea = allow_max_smem((const void *)k)) {
+        *err = ea;
+        return true;
+    }
+    k<<<persistent_grid(p, k, nw * 32, smem), nw * 32, smem, p.stream>>>(a, (int)warp_bytes);
+    *err = cudaGetLastError();
+    return true;
+}
+
+template <typename T, int W, int M2>
+bool launch_iplanes3(Plan &p, const KArgs<T> &a, cudaError_t *err)
+{
+    const size_t warp_bytes = iplanes3_bytes<W, M2>(a.m1);
+    int nw = 4;
+    while (nw > 0 && (size_t)nw * warp_bytes > (size_t)p.smem_optin) --nw;
+    if (nw < 2) return false;
+    const size_t smem = warp_bytes * nw;
+    auto k = interp_planes3_kernel<T, W, M2>;
     if (cudaError_t ea = allow_max_smem((const void *)k)) {
         *err = ea;
         return true;
@@ -1705,6 +2154,14 @@ cudaError_t interp_w(Plan &p, void *c)
     a.cout = reinterpret_cast<typename cplx<T>::type *>(c);
     const int threads = p.threads;
     count_launch();
+    if constexpr (DIM == 3 && sizeof(T) == 4 && W <= 8) {
+        const int variant = sweep_variant(p);
+        if (variant == 5 || variant == 6) {
+            cudaError_t e = cudaSuccess;
+            if (variant == 5 ? launch_iplanes3<T, W, 1>(p, a, &e) : launch_iplanes3<T, W, 2>(p, a, &e))
+                return e;
+        }
+    }
     if (p.method == NUFFT_METHOD_SM && DIM == 2) {
         // one padded bin per warp, as many warps per CTA as shared memory allows
         const int tile = a.p0 * a.p1;
@@ -1770,21 +2227,24 @@ cudaError_t spread_multi_w(const MultiLaunch &ml)
             if (ml.variant == 16) return launch(spread_sweep2_multi_kernel<T, W, 16>, (int)wb);
             return launch(spread_sweep2_multi_kernel<T, W, 32>, (int)wb);
         } else if constexpr (sizeof(T) == 4 && W <= 8) {
-            const size_t wb = sweep3_bytes<T, W, 2, 32>(ml.m1max);
-            const size_t per = args_slot<T>() + wb;
-            int nw = 4;
-            while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
-            const size_t smem = per * nw;
-            auto launch = [&](auto k) -> cudaError_t {
+            // the group's widest row range bounds every member's staging
+            auto launch = [&](auto k, size_t wb, int threads) -> cudaError_t {
+                const size_t per = args_slot<T>() + wb;
+                int nw = threads / 32;
+                while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
+                const size_t smem = per * nw;
                 if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
                 k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
                     args, ml.workoff, ml.nplans, (int)wb);
                 return cudaGetLastError();
             };
-            if (ml.variant == 1) return launch(spread_sweep3_multi_kernel<T, W, 1, 32>);
-            if (ml.variant == 2) return launch(spread_sweep3_multi_kernel<T, W, 2, 32>);
-            if (ml.variant == 5) return launch(spread_sweep3_multi_kernel<T, W, 1, 16>);
-            return launch(spread_sweep3_multi_kernel<T, W, 2, 16>);
+            if (ml.variant == 1)
+                return launch(spread_sweep3_multi_kernel<T, W, 1, 32>, sweep3_bytes<T, W, 1, 32>(ml.m1max), 128);
+            if (ml.variant == 2)
+                return launch(spread_sweep3_multi_kernel<T, W, 2, 32>, sweep3_bytes<T, W, 2, 32>(ml.m1max), 128);
+            if (ml.variant == 5)
+                return launch(spread_sweep3_multi_kernel<T, W, 1, 16>, planes3_bytes<W, 1>(ml.m1max), 128);
+            return launch(spread_sweep3_multi_kernel<T, W, 2, 16>, planes3_bytes<W, 2>(ml.m1max), 128);
         }
     }
     if (ml.method == NUFFT_METHOD_GM) {
@@ -1810,6 +2270,24 @@ cudaError_t interp_multi_w(const MultiLaunch &ml)
     using C = typename cplx<T>::type;
     const auto *args = reinterpret_cast<const KArgs<T> *>(ml.args);
     count_launch();
+    if constexpr (DIM == 3 && sizeof(T) == 4 && W <= 8) {
+        if (ml.method == NUFFT_METHOD_SM && (ml.variant == 5 || ml.variant == 6)) {
+            const size_t wb = ml.variant == 5 ? iplanes3_bytes<W, 1>(ml.m1max)
+                                              : iplanes3_bytes<W, 2>(ml.m1max);
+            const size_t per = args_slot<T>() + wb;
+            int nw = 4;
+            while (nw > 1 && (size_t)nw * per > ml.smem_optin) --nw;
+            const size_t smem = per * nw;
+            auto launch = [&](auto k) -> cudaError_t {
+                if (cudaError_t ea = allow_max_smem((const void *)k)) return ea;
+                k<<<multi_grid(k, nw * 32, smem, ml.num_sms), nw * 32, smem, ml.stream>>>(
+                    args, ml.workoff, ml.nplans, (int)wb);
+                return cudaGetLastError();
+            };
+            return ml.variant == 5 ? launch(interp_planes3_multi_kernel<T, W, 1>)
+                                   : launch(interp_planes3_multi_kernel<T, W, 2>);
+        }
+    }
     if (ml.method == NUFFT_METHOD_SM && DIM == 2) {
         const size_t wb = interp2_warp_bytes<T>(ml.tile, 1);
         const size_t per = args_slot<T>() + wb;

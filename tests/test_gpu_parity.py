@@ -213,8 +213,9 @@ def test_sweep_spread_matches_oracle(nb, bins, msub, eps, prec, kind, nt):
 
 
 # 3D single-precision shared-memory spreading runs as a register row sweep for
-# w <= 8 and bins one or two cells deep in z; widths, depths, clustered points
-# and small M_sub against the oracle's spread.
+# w <= 8 and bins one or two cells deep in z (padded width <= 16: the
+# plane-split form; up to 32: the 32-lane form); widths, depths, clustered
+# points and small M_sub against the oracle's spread.
 @pytest.mark.parametrize("bins,msub,eps,kind,nt", [
     ((16, 16, 2), 1024, 1e-6, "rand", 1),      # w = 7
     ((16, 8, 1), 128, 1e-5, "cluster", 1),     # w = 6, m2 = 1, many subproblems per bin
@@ -222,6 +223,10 @@ def test_sweep_spread_matches_oracle(nb, bins, msub, eps, prec, kind, nt):
     ((8, 16, 2), 64, 1e-4, "rand", 1),         # w = 5, 16-lane sub-warps
     ((9, 16, 2), 256, 1e-6, "gauss", 1),       # w = 7, 16-lane sub-warps
     ((13, 8, 1), 96, 1e-2, "cluster", 1),      # w = 3, 16-lane sub-warps, m2 = 1
+    ((9, 32, 1), 1024, 1e-6, "rand", 1),       # w = 7, plane-split default shape (PZ = 8)
+    ((9, 24, 1), 3000, 1e-6, "cluster", 2),    # w = 7, sweeps in pieces (clustered), ntransf 2
+    ((10, 16, 2), 128, 1e-5, "gauss", 1),      # w = 6, PZ = 8
+    ((12, 16, 1), 512, 1e-3, "rand", 1),       # w = 4, PZ = 5: odd plane share per half
 ])
 def test_sweep3_spread_matches_oracle(nb, bins, msub, eps, kind, nt):
     N = (26, 22, 20)
@@ -237,6 +242,35 @@ def test_sweep3_spread_matches_oracle(nb, bins, msub, eps, kind, nt):
         ref = oracle.spread([q.astype(np.float64) for q in pts],
                             (c[t] if nt > 1 else c).astype(np.complex128), nf, w, beta)
         assert oracle.rel_l2(g[t] if nt > 1 else g, ref) < _tol(0)
+    p.close()
+
+
+# 3D single-precision type 2 with bins of padded width <= 16 and depth 1 or 2
+# interpolates with the plane-split row sweep (padded bin in registers); the
+# whole transform against the oracle's pipeline at the same width, and the
+# exact sums.
+@pytest.mark.parametrize("bins,msub,eps,kind,nt", [
+    ((9, 64, 1), 1024, 1e-6, "rand", 1),       # w = 7, the default shape
+    ((9, 24, 1), 3000, 1e-6, "cluster", 2),    # w = 7, sweeps in pieces, ntransf 2
+    ((10, 16, 2), 128, 1e-5, "gauss", 1),      # w = 6, PZ = 8
+    ((12, 16, 1), 512, 1e-3, "rand", 1),       # w = 4, PZ = 5
+    ((13, 8, 1), 96, 1e-2, "cluster", 1),      # w = 3, PZ = 4
+    ((9, 16, 2), 256, 1e-6, "rand", 1),        # w = 7, PZ = 9: one unused plane
+])
+def test_sweep3_interp_matches_oracle(nb, bins, msub, eps, kind, nt):
+    N = (26, 22, 20)
+    M = 9001
+    p = _plan(nb, 2, N, eps, 0, method="sm", bins=bins, msub=msub, ntransf=nt)
+    w, nf = p.params["w"], p.params["nf"][:3]
+    pts = wl.points(kind, 3, M, 41 + bins[0], np.float32, n=nf, spread=0.3)
+    f = wl.modes(N, 42, np.complex64, ntransf=nt)
+    p.setpts(*_pts_dev(pts, 0))
+    c = _host(p.execute(f=_dev(f)))
+    p64 = [q.astype(np.float64) for q in pts]
+    for t in range(nt):
+        ft = (f[t] if nt > 1 else f).astype(np.complex128)
+        ref = oracle.nufft_type2(p64, ft, w=w)
+        assert oracle.rel_l2(c[t] if nt > 1 else c, ref) < _tol(0)
     p.close()
 
 
