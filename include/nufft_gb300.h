@@ -94,10 +94,10 @@ void nufft_default_opts(nufft_opts *opts);
 
 /*
  * Create a plan (Sec. 1.1 "plan"; parameters of Sec. 3).
- *   type    1 or 2.
+ *   type    1 or 2; 3 for nonuniform-to-nonuniform (see nufft_setpts3).
  *   dim     1, 2 or 3 (1D is the d = 1 case of Sec. 3, which the paper lists as
  *           future work: bins of m1 cells, the same three methods).
- *   nmodes  dim entries N1 (, N2 (, N3)), each >= 1.
+ *   nmodes  dim entries N1 (, N2 (, N3)), each >= 1 (ignored, may be NULL, for type 3).
  *   iflag   +1 or -1: sign of the type 1 exponent (type 2 uses the opposite).
  *   ntransf number of strength / coefficient vectors per execute (>= 1).
  *   eps     requested relative tolerance; kernel width w = ceil(log10(1/eps)) + 1
@@ -127,9 +127,30 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
 int nufft_setpts(nufft_plan plan, int64_t M, const void *x, const void *y, const void *z);
 
 /*
+ * Type 3 points and frequencies (the nonuniform-to-nonuniform transform the
+ * paper lists as future work):
+ *   f_k = sum_j c_j exp(i iflag s_k . x_j),  j < M, k < K,
+ * x_j = (x, y, z)_j and s_k = (s, t, u)_k real and of any range (device arrays
+ * of the plan precision; y / t NULL in 1D, z / u NULL in 1D and 2D).  The call
+ * reads the extents of both sets (X_i and S_i, the half-widths about their
+ * centres; it synchronizes the plan's stream for that), sizes a spreading grid
+ * of n_i = smallest even 2^a 3^b 5^c >= max(4 S_i X_i / pi + w + 2, 2w) cells,
+ * and sets up two inner plans of this library: the type 1 spreading step on
+ * that grid for the rescaled points, and a type 2 transform of the grid at the
+ * rescaled frequencies.  Only for plans made with type 3; upsampfac 2.
+ * Errors: NUFFT_ERR_ARG (wrong plan type, null arrays, non-finite coordinates),
+ * NUFFT_ERR_SIZE (S_i X_i too large), NUFFT_ERR_ALLOC.
+ */
+int nufft_setpts3(nufft_plan plan, int64_t M, const void *x, const void *y, const void *z,
+                  int64_t K, const void *s, const void *t, const void *u);
+
+/*
  * Execute (Sec. 1.1 "execute"; Sec. 3.1 for type 1, Sec. 3.2 for type 2).
  *   type 1: reads c (ntransf*M complex), overwrites f (ntransf*N complex).
  *   type 2: reads f, overwrites c.
+ *   type 3: reads c (ntransf*M complex), overwrites f (ntransf*K complex).
+ * The stage entry points below, nufft_execute_host, nufft_get_finegrid,
+ * nufft_get_sort and batches take type 1 and type 2 plans only.
  */
 int nufft_execute(nufft_plan plan, void *c, void *f);
 
@@ -259,7 +280,7 @@ int nufft_tune_cache_clear(void);
  * (GM: chunks of points) of all its plans; clears, corrections and cuFFT stay
  * per plan.
  *
- * nufft_batch_create: plans[0..nplans) must be distinct and set up (setpts)
+ * nufft_batch_create: plans[0..nplans) must be distinct type 1 / 2 plans, set up (setpts)
  *   before each execute; while the batch exists they run on `stream` (their cuFFT
  *   plans are re-bound to it) and must not be used on their own.  Destroying the
  *   batch hands them back their own streams.

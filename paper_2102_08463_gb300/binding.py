@@ -41,7 +41,7 @@ EXPORTS = (
     "nufft_picker_load", "nufft_picker_predict", "nufft_picker_grad", "nufft_picker_step",
     "nufft_picker_train", "nufft_picker_loss", "nufft_picker_install", "nufft_picker_features",
     "nufft_point_skew", "nufft_fma_peak", "nufft_execute_host", "nufft_get_status",
-    "nufft_debug_fail",
+    "nufft_debug_fail", "nufft_setpts3",
 )
 
 PICKER_NFEAT = 12
@@ -106,6 +106,7 @@ def load():
         lib.nufft_makeplan.argtypes = [I, I, ctypes.POINTER(I64), I, I, ctypes.c_double, I,
                                        ctypes.POINTER(Opts), ctypes.POINTER(P)]
         lib.nufft_setpts.argtypes = [P, I64, P, P, P]
+        lib.nufft_setpts3.argtypes = [P, I64, P, P, P, I64, P, P, P]
         lib.nufft_execute.argtypes = [P, P, P]
         lib.nufft_destroy.argtypes = [P]
         lib.nufft_strerror.argtypes = [I]
@@ -226,6 +227,11 @@ def makeplan(type_, dim, nmodes, iflag=+1, ntransf=1, eps=1e-6, prec=-1, opts=No
 
 def setpts(h, M, x, y, z=None):
     _check(load().nufft_setpts(ctypes.c_void_p(h), int(M), x, y, z), "nufft_setpts")
+
+
+def setpts3(h, M, x, y, z, K, s, t, u):
+    _check(load().nufft_setpts3(ctypes.c_void_p(h), int(M), x, y, z, int(K), s, t, u),
+           "nufft_setpts3")
 
 
 def execute(h, c, f):
@@ -707,3 +713,64 @@ class _DeviceView:
             "version": 3,
             "strides": None,
         }
+
+
+class Plan3:
+    """Type 3 plan (nonuniform points to nonuniform frequencies):
+    f_k = sum_j c_j exp(i iflag s_k . x_j).
+
+    Plan3(dim, eps, iflag=+1, ntransf=1, prec=-1, stream=None); setpts(xs, ss) with
+    xs / ss lists of dim real device tensors (M points, K frequencies);
+    execute(c) -> f of shape ([ntransf,] K).
+    """
+
+    def __init__(self, dim, eps, iflag=+1, ntransf=1, prec=-1, stream=None, debug_checks=False):
+        import torch
+        self._torch = torch
+        self.dim = int(dim)
+        self.ntransf = int(ntransf)
+        o = default_opts()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o.stream = ctypes.c_void_p(stream.cuda_stream)
+        o.debug_checks = 1 if debug_checks else 0
+        self.handle = None
+        self.handle = makeplan(3, self.dim, [1] * self.dim, iflag, ntransf, eps, prec, o)
+        self.params = get_params(self.handle)
+        self.real_dtype = torch.float32 if self.params["prec"] == 0 else torch.float64
+        self.complex_dtype = torch.complex64 if self.params["prec"] == 0 else torch.complex128
+        self.M = self.K = 0
+        self._keep = None
+
+    def setpts(self, xs, ss):
+        rd = self.real_dtype
+        if len(xs) != self.dim or len(ss) != self.dim:
+            raise ValueError("need %d coordinate arrays for points and for frequencies" % self.dim)
+        M, K = xs[0].shape[0], ss[0].shape[0]
+        xp = [_dptr(a, rd, "x") for a in xs] + [None] * (3 - self.dim)
+        sp = [_dptr(a, rd, "s") for a in ss] + [None] * (3 - self.dim)
+        setpts3(self.handle, M, xp[0], xp[1], xp[2], K, sp[0], sp[1], sp[2])
+        self.M, self.K = M, K
+        self._keep = (xs, ss)
+        self.params = get_params(self.handle)   # the spreading grid sizes (nf)
+
+    def execute(self, c, f=None):
+        torch = self._torch
+        shp = (self.K,) if self.ntransf == 1 else (self.ntransf, self.K)
+        if f is None:
+            f = torch.empty(shp, dtype=self.complex_dtype, device="cuda")
+        cd = self.complex_dtype
+        execute(self.handle, _dptr(c, cd, "c"), _dptr(f, cd, "f"))
+        return f
+
+    def close(self):
+        if self.handle:
+            destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -224,7 +224,7 @@ int nufft_batch_create(const nufft_plan *plans, int nplans, void *stream, nufft_
     *out = nullptr;
     if (!plans || nplans < 1) return NUFFT_ERR_ARG;
     for (int k = 0; k < nplans; ++k) {
-        if (!plans[k]) return NUFFT_ERR_ARG;
+        if (!plans[k] || plans[k]->p.type == 3) return NUFFT_ERR_ARG;   // types 1 and 2
         for (int j = 0; j < k; ++j)
             if (plans[j] == plans[k]) return NUFFT_ERR_ARG;
     }

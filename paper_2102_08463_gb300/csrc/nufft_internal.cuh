@@ -193,6 +193,8 @@ __device__ __forceinline__ void atomic_add_cplx(double2 *p, double re, double im
 // ---------------------------------------------------------------------------
 // Plan object (Sec. 1.1 plan / setup / execute / destroy).
 // ---------------------------------------------------------------------------
+struct Type3;   // type 3 state (type3.cu)
+
 struct Plan {
     int type = 1, dim = 2, iflag = 1, ntransf = 1, prec = 0;
     double eps = 1e-6, sigma = 2.0, beta = 0.0;
@@ -257,6 +259,8 @@ struct Plan {
     int64_t hx_cap = 0;            // points the staging holds
     cudaStream_t hx_copy = nullptr;   // stream of the input copy
     cudaEvent_t hx_ev[2] = {nullptr, nullptr};   // entry, input copied
+
+    Type3 *t3 = nullptr;           // type 3 plans: inner plans and per-point factors
 };
 
 // Tile settings of a plan (method, bin sizes, subproblem cap, threads per CTA).
@@ -288,6 +292,30 @@ int picker_choose(Plan &p, int64_t M, const void *x, const void *y, const void *
                   bool *chosen);
 // Parameter rules of Sec. 3 shared by makeplan and the picker's features.
 int next235(int64_t n);
+// Device allocation (NUFFT_ERR_ALLOC on failure, honouring nufft_debug_fail) and
+// the CUDA-to-NUFFT error mapping shared by the host code.
+int cuda_err(cudaError_t e);
+int dev_alloc_raw(void **ptr, size_t bytes);
+template <typename Ptr>
+inline int dev_alloc(Ptr **ptr, size_t bytes)
+{
+    void *v = nullptr;
+    const int rc = dev_alloc_raw(&v, bytes);
+    *ptr = reinterpret_cast<Ptr *>(v);
+    return rc;
+}
+void dev_free(void *ptr);
+// Gauss-Legendre nodes and weights on [-1, 1].
+void gauss_legendre(int nq, std::vector<double> &x, std::vector<double> &wt);
+// Frees the cuFFT plan of a plan used for spreading only.
+void plan_drop_fft(Plan &p);
+// Type 3 (type3.cu): state set-up at makeplan, points and frequencies, execute,
+// release, and the size of its spreading grid.
+int type3_init(Plan &p, const nufft_opts &o);
+void type3_free(Plan &p);
+int type3_setpts(Plan &p, int64_t M, const void *const *x, int64_t K, const void *const *s);
+int type3_execute(Plan &p, const void *c, void *f);
+void type3_grid(const Plan &p, int64_t *n);
 int kernel_width(double eps, double sigma);
 
 // Launchers implemented in the .cu files.  All enqueue on p.stream and return a

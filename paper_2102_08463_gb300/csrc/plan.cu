@@ -98,61 +98,6 @@ double kernel_beta(int w, double sigma)
     return sigma == 2.0 ? 2.30 * w : 2.30 * w * (1.0 - 1.0 / (2.0 * sigma)) / 0.75;
 }
 
-// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_nq.
-void gauss_legendre(int nq, std::vector<double> &x, std::vector<double> &wt)
-{
-    const double PI = 3.14159265358979323846;
-    x.assign(nq, 0.0);
-    wt.assign(nq, 0.0);
-    for (int i = 0; i < nq; ++i) {
-        double z = cos(PI * (i + 0.75) / (nq + 0.5));
-        double dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = z;
-            for (int k = 2; k <= nq; ++k) {
-                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = pk;
-            }
-            // p1 = P_nq(z), p0 = P_{nq-1}(z)
-            dp = nq * (z * p1 - p0) / (z * z - 1.0);
-            double dz = p1 / dp;
-            z -= dz;
-            if (fabs(dz) < 1e-16) break;
-        }
-        x[i] = z;
-        wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-    }
-}
-
-int cuda_err(cudaError_t e)
-{
-    if (e == cudaSuccess) return NUFFT_OK;
-    if (e == cudaErrorMemoryAllocation) return NUFFT_ERR_ALLOC;
-    return NUFFT_ERR_CUDA;
-}
-
-template <typename Ptr>
-int dev_alloc(Ptr **ptr, size_t bytes)
-{
-    *ptr = nullptr;
-    if (injected_failure(NUFFT_FAIL_ALLOC)) return NUFFT_ERR_ALLOC;
-    if (bytes == 0) bytes = 16;
-    void *v = nullptr;
-    cudaError_t e = cudaMalloc(&v, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();   // clear the sticky-free allocation error
-        return NUFFT_ERR_ALLOC;
-    }
-    *ptr = reinterpret_cast<Ptr *>(v);
-    return NUFFT_OK;
-}
-
-void dev_free(void *ptr)
-{
-    if (ptr) cudaFree(ptr);
-}
-
 void free_points(Plan &p)
 {
     dev_free(p.keys);
@@ -185,6 +130,7 @@ void free_host_staging(Plan &p)
 
 void free_plan(Plan &p)
 {
+    type3_free(p);
     free_points(p);
     free_host_staging(p);
     dev_free(p.hx_f);
@@ -222,6 +168,67 @@ int default_method(const Plan &p, size_t smem_limit)
 }
 
 }  // namespace
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_nq.
+void nufft::gauss_legendre(int nq, std::vector<double> &x, std::vector<double> &wt)
+{
+    const double PI = 3.14159265358979323846;
+    x.assign(nq, 0.0);
+    wt.assign(nq, 0.0);
+    for (int i = 0; i < nq; ++i) {
+        double z = cos(PI * (i + 0.75) / (nq + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= nq; ++k) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            // p1 = P_nq(z), p0 = P_{nq-1}(z)
+            dp = nq * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+int nufft::cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess) return NUFFT_OK;
+    if (e == cudaErrorMemoryAllocation) return NUFFT_ERR_ALLOC;
+    return NUFFT_ERR_CUDA;
+}
+
+int nufft::dev_alloc_raw(void **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (injected_failure(NUFFT_FAIL_ALLOC)) return NUFFT_ERR_ALLOC;
+    if (bytes == 0) bytes = 16;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free allocation error
+        return NUFFT_ERR_ALLOC;
+    }
+    *ptr = v;
+    return NUFFT_OK;
+}
+
+void nufft::dev_free(void *ptr)
+{
+    if (ptr) cudaFree(ptr);
+}
+
+// Frees the cuFFT plan (and its work area) of a plan that will only spread.
+void nufft::plan_drop_fft(Plan &p)
+{
+    if (p.fft_ready) cufftDestroy(p.fft);
+    p.fft_ready = false;
+}
 
 // Interior window cell i of a width-w kernel as a function of s in [-1, 1]:
 // g_i(s) = phi_beta((i + 1 - w/2 - t) 2 / w), t = (s + 1) / 2 (Sec. 3 Eq. (es)).
@@ -378,7 +385,7 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
 {
     if (!out) return NUFFT_ERR_ARG;
     *out = nullptr;
-    if ((type != 1 && type != 2) || dim < 1 || dim > 3 || !nmodes) return NUFFT_ERR_ARG;
+    if (type < 1 || type > 3 || dim < 1 || dim > 3 || (type != 3 && !nmodes)) return NUFFT_ERR_ARG;
     if (iflag != 1 && iflag != -1) return NUFFT_ERR_ARG;
     if (ntransf < 1 || prec < -1 || prec > 1) return NUFFT_ERR_ARG;
     if (!(eps > 0.0) || !isfinite(eps)) return NUFFT_ERR_EPS;
@@ -399,6 +406,37 @@ int nufft_makeplan(int type, int dim, const int64_t *nmodes, int iflag, int ntra
     if (prec == 0 && eps < fp32_floor) return NUFFT_ERR_EPS;
     int w = kernel_width(eps, sigma);
     if (w > kMaxW) return NUFFT_ERR_EPS;
+    if (type == 3) {
+        // type 3: the grids depend on the points and frequencies, so the inner
+        // plans are made at setpts (nufft_setpts3); sigma = 2 only
+        if (sigma != 2.0) return NUFFT_ERR_ARG;
+        nufft_plan_s *h3 = new (std::nothrow) nufft_plan_s;
+        if (!h3) return NUFFT_ERR_ALLOC;
+        Plan &q = h3->p;
+        q.type = 3;
+        q.dim = dim;
+        q.iflag = iflag;
+        q.ntransf = ntransf;
+        q.prec = prec;
+        q.eps = eps;
+        q.sigma = sigma;
+        q.w = w;
+        q.beta = kernel_beta(w, sigma);
+        q.stream = (cudaStream_t)o.stream;
+        q.debug_checks = o.debug_checks != 0;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&q.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (q.num_sms < 1) q.num_sms = 1;
+        const int rc = type3_init(q, o);
+        if (rc != NUFFT_OK) {
+            free_plan(q);
+            delete h3;
+            return rc;
+        }
+        *out = h3;
+        return NUFFT_OK;
+    }
 
     nufft_plan_s *h = new (std::nothrow) nufft_plan_s;
     if (!h) return NUFFT_ERR_ALLOC;
@@ -560,6 +598,7 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
 {
     if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
+    if (p.type == 3) return NUFFT_ERR_ARG;   // nufft_setpts3
     if (M < 0 || M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_ARG;
     if (M > 0 && (!x || (p.dim >= 2 && !y) || (p.dim == 3 && !z))) return NUFFT_ERR_ARG;
     p.have_pts = false;
@@ -652,8 +691,24 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
     return NUFFT_OK;
 }
 
+int nufft_setpts3(nufft_plan h, int64_t M, const void *x, const void *y, const void *z, int64_t K,
+                  const void *s, const void *t, const void *u)
+{
+    if (!h) return NUFFT_ERR_ARG;
+    Plan &p = h->p;
+    if (p.type != 3) return NUFFT_ERR_ARG;
+    if (M < 0 || M >= ((int64_t)1 << 31) - 1 || K < 0 || K >= ((int64_t)1 << 31) - 1)
+        return NUFFT_ERR_ARG;
+    if (M > 0 && (!x || (p.dim >= 2 && !y) || (p.dim == 3 && !z))) return NUFFT_ERR_ARG;
+    if (K > 0 && (!s || (p.dim >= 2 && !t) || (p.dim == 3 && !u))) return NUFFT_ERR_ARG;
+    p.have_pts = false;
+    const void *xs[3] = {x, y, z}, *ss[3] = {s, t, u};
+    return type3_setpts(p, M, xs, K, ss);
+}
+
 int nufft_spread(nufft_plan h, const void *c)
 {
+    if (h && h->p.type == 3) return NUFFT_ERR_ARG;   // stages of types 1 and 2
     if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
     if (!p.have_pts) return NUFFT_ERR_NOPTS;
@@ -665,6 +720,7 @@ int nufft_spread(nufft_plan h, const void *c)
 
 int nufft_spread_add(nufft_plan h, const void *c)
 {
+    if (h && h->p.type == 3) return NUFFT_ERR_ARG;   // stages of types 1 and 2
     if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
     if (!p.have_pts) return NUFFT_ERR_NOPTS;
@@ -683,6 +739,7 @@ int nufft_spread_add(nufft_plan h, const void *c)
 
 int nufft_interp(nufft_plan h, void *c)
 {
+    if (h && h->p.type == 3) return NUFFT_ERR_ARG;   // stages of types 1 and 2
     if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
     if (!p.have_pts) return NUFFT_ERR_NOPTS;
@@ -698,6 +755,7 @@ int nufft_interp(nufft_plan h, void *c)
 
 int nufft_fft(nufft_plan h)
 {
+    if (h && h->p.type == 3) return NUFFT_ERR_ARG;   // stages of types 1 and 2
     if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
     // type 1 FFT takes the sign of iflag, type 2 the opposite (Eq. 2d1 / 2d2)
@@ -713,12 +771,14 @@ int nufft_fft(nufft_plan h)
 
 int nufft_deconvolve(nufft_plan h, void *f)
 {
+    if (h && h->p.type == 3) return NUFFT_ERR_ARG;   // stages of types 1 and 2
     if (!h || !f) return NUFFT_ERR_ARG;
     return cuda_err(launch_deconvolve(h->p, f));
 }
 
 int nufft_precorrect(nufft_plan h, const void *f)
 {
+    if (h && h->p.type == 3) return NUFFT_ERR_ARG;   // stages of types 1 and 2
     if (!h || !f) return NUFFT_ERR_ARG;
     return cuda_err(launch_precorrect(h->p, f));
 }
@@ -729,6 +789,7 @@ int nufft_execute(nufft_plan h, void *c, void *f)
     Plan &p = h->p;
     if (!p.have_pts) return NUFFT_ERR_NOPTS;
     if (p.M > 0 && !c) return NUFFT_ERR_ARG;
+    if (p.type == 3) return type3_execute(p, c, f);
     int rc;
     if (p.type == 1) {
         if ((rc = nufft_spread(h, c)) != NUFFT_OK) return rc;
@@ -745,6 +806,7 @@ int nufft_execute_host(nufft_plan h, int64_t M, const void *x, const void *y, co
 {
     if (!h || !f) return NUFFT_ERR_ARG;
     Plan &p = h->p;
+    if (p.type == 3) return NUFFT_ERR_ARG;
     if (M < 0 || M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_ARG;
     if (M > 0 && (!x || (p.dim >= 2 && !y) || (p.dim == 3 && !z) || !c)) return NUFFT_ERR_ARG;
     const size_t rs = real_size(p), cs = 2 * rs;
@@ -825,8 +887,10 @@ int nufft_get_params(nufft_plan h, int *w, double *beta, int64_t *nf, int *bins,
     const Plan &p = h->p;
     if (w) *w = p.w;
     if (beta) *beta = p.beta;
+    int64_t g3[3] = {1, 1, 1};
+    if (p.type == 3) type3_grid(p, g3);
     for (int d = 0; d < 3; ++d) {
-        if (nf) nf[d] = p.nf[d];
+        if (nf) nf[d] = p.type == 3 ? g3[d] : p.nf[d];
         if (bins) bins[d] = p.m[d];
     }
     if (nbins) *nbins = p.nbins;
@@ -837,6 +901,7 @@ int nufft_get_params(nufft_plan h, int *w, double *beta, int64_t *nf, int *bins,
 
 int nufft_get_finegrid(nufft_plan h, void **dptr, size_t *bytes)
 {
+    if (h && h->p.type == 3) return NUFFT_ERR_ARG;   // stages of types 1 and 2
     if (!h) return NUFFT_ERR_ARG;
     const Plan &p = h->p;
     if (dptr) *dptr = p.fine;
@@ -880,6 +945,7 @@ int nufft_get_sort(nufft_plan h, int32_t *t, int32_t *bincounts, int32_t *nsub)
 {
     if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
+    if (p.type == 3) return NUFFT_ERR_ARG;
     if (!p.have_pts) return NUFFT_ERR_NOPTS;
     if (p.method == NUFFT_METHOD_GM) return NUFFT_ERR_METHOD;
     cudaError_t e = cudaSuccess;
