@@ -180,14 +180,16 @@ __device__ __forceinline__ int wrap_index(int l, int n)
 // Atomic complex add into global memory as reductions (no value returned, so
 // the issuing warp does not wait for the L2 round trip): one 8-byte vector
 // reduction for single precision (sm_90+), two 8-byte ones for double.
+// No memory clobber: no kernel reads the grid it reduces into, so the compiler
+// may schedule other loads and stores around the reductions.
 __device__ __forceinline__ void atomic_add_cplx(float2 *p, float re, float im)
 {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(re), "f"(im) : "memory");
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(re), "f"(im));
 }
 __device__ __forceinline__ void atomic_add_cplx(double2 *p, double re, double im)
 {
-    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->x), "d"(re) : "memory");
-    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->y), "d"(im) : "memory");
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->x), "d"(re));
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->y), "d"(im));
 }
 
 // ---------------------------------------------------------------------------
@@ -227,6 +229,8 @@ struct Plan {
     int32_t *vals = nullptr;       // [Mcap]
     int32_t *vals_alt = nullptr;   // [Mcap]
     int32_t *perm = nullptr;       // [Mcap] t: sorted position -> original index
+    int32_t *rorder = nullptr;     // [Mcap] 3D: record position -> original index
+    bool row_ordered = false;      // records ordered by start row inside each subproblem
     void *recs = nullptr;          // [Mcap] rec4<T> per point, in t order (see setpts.cu)
     void *xyz_copy[3] = {nullptr, nullptr, nullptr};  // coordinate copies for GM
     int32_t *bincount = nullptr;   // [nbins]
@@ -373,6 +377,10 @@ struct MultiLaunch {
 // (padded width <= 16).  Type 2: m2 + 4 for the 3D plane-split interpolation.
 // 0 if the plan uses the shared-memory kernels.
 int sweep_variant(const Plan &p);
+// m2 + 4 if the plan's shape suits the 3D plane-split sweeps (single precision,
+// SM, w <= 8, padded width <= 16, m2 in {1, 2}), else 0; setpts orders such a
+// plan's records by start row and sweep_variant then reports the form.
+int planes3_form(const Plan &p);
 cudaError_t spread_multi_f32_1d(const MultiLaunch &ml);
 cudaError_t spread_multi_f64_1d(const MultiLaunch &ml);
 cudaError_t interp_multi_f32_1d(const MultiLaunch &ml);

@@ -105,6 +105,9 @@ void free_points(Plan &p)
     dev_free(p.vals);
     dev_free(p.vals_alt);
     dev_free(p.recs);
+    dev_free(p.rorder);
+    p.rorder = nullptr;
+    p.row_ordered = false;
     dev_free(p.subprob);
     for (int d = 0; d < 3; ++d) {
         dev_free(p.xyz_copy[d]);
@@ -287,17 +290,26 @@ void nufft::fit_kernel_poly(Plan &p)
     p.poly_ok = worst <= fmax(p.eps * 1e-3, p.prec == 0 ? 3e-8 : 1e-14);
 }
 
+int nufft::planes3_form(const Plan &p)
+{
+    if (p.method != NUFFT_METHOD_SM || p.dim != 3 || p.prec != 0 || p.w > 8) return 0;
+    const int p0 = padded(p.m[0], p.w);
+    return p0 <= 16 && (p.m[2] == 1 || p.m[2] == 2) ? p.m[2] + 4 : 0;
+}
+
 int nufft::sweep_variant(const Plan &p)
 {
     if (p.method != NUFFT_METHOD_SM) return 0;
     const int p0 = padded(p.m[0], p.w);
-    if (p.type == 2)   // the plane-split interpolation sweep (3D single, p0 <= 16)
-        return p.dim == 3 && p.prec == 0 && p.w <= 8 && p0 <= 16 && (p.m[2] == 1 || p.m[2] == 2)
-                   ? p.m[2] + 4 : 0;
-    if (p0 > 32) return 0;
-    if (p.dim == 2) return p0 <= 8 ? 8 : (p0 <= 16 ? 16 : 32);
-    if (p.prec == 0 && p.w <= 8 && (p.m[2] == 1 || p.m[2] == 2)) return p.m[2] + (p0 <= 16 ? 4 : 0);
-    return 0;
+    if (p.dim == 3) {
+        // the plane-split sweeps read records ordered by start row (setpts)
+        const int f = planes3_form(p);
+        if (f) return p.row_ordered ? f : 0;
+        if (p.type == 2) return 0;
+        return p0 <= 32 && p.prec == 0 && p.w <= 8 && (p.m[2] == 1 || p.m[2] == 2) ? p.m[2] : 0;
+    }
+    if (p.type != 1 || p.dim != 2 || p0 > 32) return 0;
+    return p0 <= 8 ? 8 : (p0 <= 16 ? 16 : 32);
 }
 
 bool nufft::tiles_feasible(const Plan &p, const Tiles &t)
@@ -599,6 +611,7 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
     if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
     if (p.type == 3) return NUFFT_ERR_ARG;   // nufft_setpts3
+    p.row_ordered = false;
     if (M < 0 || M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_ARG;
     if (M > 0 && (!x || (p.dim >= 2 && !y) || (p.dim == 3 && !z))) return NUFFT_ERR_ARG;
     p.have_pts = false;
@@ -627,6 +640,7 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
         if (rc == NUFFT_OK) rc = dev_alloc(&p.vals, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.vals_alt, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.recs, rsz * cap);
+        if (rc == NUFFT_OK && p.dim == 3) rc = dev_alloc(&p.rorder, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.subprob, sizeof(int4) * maxsub);
         if (rc != NUFFT_OK) {
             free_points(p);
@@ -785,11 +799,12 @@ int nufft_precorrect(nufft_plan h, const void *f)
 
 int nufft_execute(nufft_plan h, void *c, void *f)
 {
-    if (!h || !f) return NUFFT_ERR_ARG;
+    if (!h) return NUFFT_ERR_ARG;
     Plan &p = h->p;
+    if (p.type == 3) return p.have_pts ? type3_execute(p, c, f) : NUFFT_ERR_NOPTS;
+    if (!f) return NUFFT_ERR_ARG;
     if (!p.have_pts) return NUFFT_ERR_NOPTS;
     if (p.M > 0 && !c) return NUFFT_ERR_ARG;
-    if (p.type == 3) return type3_execute(p, c, f);
     int rc;
     if (p.type == 1) {
         if ((rc = nufft_spread(h, c)) != NUFFT_OK) return rc;

@@ -704,6 +704,107 @@ cudaError_t launch_records(Plan &p, const T *x, const T *y, const T *z,
     return cudaGetLastError();
 }
 
+// 3D plane-split sweeps: inside every subproblem the records are put in order
+// of window start row (stable, in pieces of kRowPiece points), with the point
+// indices moved alike into rorder.  The sweeps then read each subproblem as
+// runs of ascending start rows and need no ordering of their own; t itself is
+// unchanged (rorder is a copy reordered with the records).
+constexpr int kRowPiece = 1024;
+constexpr int kRowWarps = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kRowWarps * 32)
+row_order_kernel(typename rec4<T>::type *__restrict__ recs, const int32_t *__restrict__ perm,
+                 const int4 *__restrict__ subprob, const int32_t *__restrict__ nsub, int nkeys,
+                 int32_t *__restrict__ rorder)
+{
+    using R = typename rec4<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t per_warp = (size_t)kRowPiece * (sizeof(R) + 4) + 4 * (nkeys + 1);
+    unsigned char *base = smem_raw + warp * ((per_warp + 15) & ~(size_t)15);
+    R *srec = reinterpret_cast<R *>(base);
+    int32_t *sidx = reinterpret_cast<int32_t *>(base + kRowPiece * sizeof(R));
+    int *cnt = reinterpret_cast<int *>(base + (size_t)kRowPiece * (sizeof(R) + 4));
+    const unsigned lt = (1u << lane) - 1u;
+    const int ns = *nsub;
+    for (int sp = blockIdx.x * kRowWarps + warp; sp < ns; sp += gridDim.x * kRowWarps) {
+        const int4 sub = subprob[sp];
+        for (int piece = 0; piece < sub.z; piece += kRowPiece) {
+            const int np = min(kRowPiece, sub.z - piece);
+            const int64_t b0 = (int64_t)sub.y + piece;
+            for (int i = lane; i <= nkeys; i += 32) cnt[i] = 0;
+            for (int i = lane; i < np; i += 32) {
+                srec[i] = recs[b0 + i];
+                sidx[i] = perm[b0 + i];
+            }
+            __syncwarp();
+            // counts per start row (warp-aggregated), exclusive prefix, stable scatter
+            for (int i0 = 0; i0 < np; i0 += 32) {
+                const int i = i0 + lane;
+                const int key = i < np ? (int)((unpack_word_t<T>(srec[i].w) >> 10) & 1023u) : 0x7fffffff;
+                const unsigned peers = __match_any_sync(kFull, key);
+                if (i < np && (peers & lt) == 0) atomicAdd(&cnt[key + 1], __popc(peers));
+            }
+            __syncwarp();
+            int running = 0;
+            for (int i0 = 0; i0 <= nkeys; i0 += 32) {
+                const int i = i0 + lane;
+                int v = i <= nkeys ? cnt[i] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(kFull, v, o);
+                    if (lane >= o) v += t;
+                }
+                if (i <= nkeys) cnt[i] = running + v;
+                running += __shfl_sync(kFull, v, 31);
+            }
+            __syncwarp();
+            for (int i0 = 0; i0 < np; i0 += 32) {
+                const int i = i0 + lane;
+                const int key = i < np ? (int)((unpack_word_t<T>(srec[i].w) >> 10) & 1023u) : 0x7fffffff;
+                const unsigned peers = __match_any_sync(kFull, key);
+                const int leader = __ffs(peers) - 1;
+                int pos = 0;
+                if (i < np && lane == leader) pos = atomicAdd(&cnt[key], __popc(peers));
+                pos = __shfl_sync(kFull, pos, leader) + __popc(peers & lt);
+                if (i < np) {
+                    recs[b0 + pos] = srec[i];
+                    rorder[b0 + pos] = sidx[i];
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Records (t order), then, for plans swept by the 3D plane-split kernels, their
+// order by start row inside each subproblem.
+template <typename T>
+cudaError_t finish_records(Plan &p, const T *x, const T *y, const T *z,
+                           typename rec4<T>::type *recs)
+{
+    cudaError_t e = launch_records<T>(p, x, y, z, recs);
+    p.row_ordered = false;
+    if (e != cudaSuccess || p.dim != 3 || sizeof(T) != 4) return e;
+    if (planes3_form(p) == 0) return e;
+    using R = typename rec4<T>::type;
+    const int nkeys = p.m[1] + 1;
+    const size_t per_warp = (((size_t)kRowPiece * (sizeof(R) + 4) + 4 * (nkeys + 1)) + 15) & ~(size_t)15;
+    const size_t smem = per_warp * kRowWarps;
+    auto k = row_order_kernel<T>;
+    e = allow_max_smem((const void *)k);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRowWarps * 32, smem);
+    const int grid = p.num_sms * (per_sm < 1 ? 1 : per_sm);
+    count_launch();
+    k<<<grid, kRowWarps * 32, smem, p.stream>>>(recs, p.perm, p.subprob, p.nsub, nkeys, p.rorder);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) p.row_ordered = true;
+    return e;
+}
+
 template <typename T>
 cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
 {
@@ -740,7 +841,7 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
         p.perm = p.vals;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return launch_records<T>(p, x, y, z, recs);
+        return finish_records<T>(p, x, y, z, recs);
     } else {
         const int g = grid_for(M, 256, p.num_sms);
         count_launch();
@@ -789,7 +890,7 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
         p.bincount, p.binstart, p.scan_tmp, nbins, p.msub, p.subprob);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_records<T>(p, x, y, z, recs);
+    return finish_records<T>(p, x, y, z, recs);
 }
 
 }  // namespace

@@ -869,7 +869,8 @@ template <int W, int M2> __host__ __device__ constexpr int planes3_slot()
 template <int W, int M2>
 __host__ __device__ inline size_t planes3_bytes(int m1)
 {
-    return sweep_head(m1 + 1) + sizeof(float) * (size_t)32 * planes3_slot<W, M2>();
+    (void)m1;
+    return sizeof(float) * (size_t)32 * planes3_slot<W, M2>();
 }
 
 template <typename T, int W, int M2>
@@ -885,20 +886,19 @@ __device__ __forceinline__ void spread_planes3_sub(const KArgs<T> &a, int4 sub, 
     constexpr int OWZ = planes3_owz<W, M2>(), OCX = planes3_ocx<W, M2>();
     const int lane = threadIdx.x & 31, h = lane >> 4, q = lane & 15;
     const int n = sub.z;
-    uint16_t *idx = reinterpret_cast<uint16_t *>(sm);
-    int *cnt = reinterpret_cast<int *>(sm + 2 * kSweepCap);
-    float *stg = reinterpret_cast<float *>(sm + sweep_head(a.m1 + 1));
+    float *stg = reinterpret_cast<float *>(sm);
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
     const int P = pad_lo(W);
     const C *cin = a.cin + (int64_t)tr * a.M;
-    C *grid = a.grid + (int64_t)tr * a.nftot;
     const bool xok = q < a.p0;
     const int gx = wrap_any(o0 - P + (xok ? q : 0), a.n0);
     const int grow0 = wrap_any(o1 - P, a.n1);
+    C *grid = a.grid + (int64_t)tr * a.nftot + gx;
     int gz[KZ];                                            // fine-grid plane of each owned plane
 #pragma unroll
-    for (int i = 0; i < KZ; ++i) gz[i] = wrap_any(o2 - P + h * KZ + i, a.n2);
+    for (int i = 0; i < KZ; ++i)
+        gz[i] = xok && h * KZ + i < PZ ? wrap_any(o2 - P + h * KZ + i, a.n2) : -1;
     float2 acc[KZ][W];
 #pragma unroll
     for (int i = 0; i < KZ; ++i)
@@ -910,8 +910,8 @@ __device__ __forceinline__ void spread_planes3_sub(const KArgs<T> &a, int4 sub, 
         for (int i = 0; i < KZ; ++i) {
             const float2 v = acc[i][k < W ? k : 0];
             acc[i][k < W ? k : 0] = make_float2(0.f, 0.f);
-            if (xok && h * KZ + i < PZ && (v.x != 0.f || v.y != 0.f))
-                atomic_add_cplx(&grid[((int64_t)gz[i] * a.n1 + g) * a.n0 + gx], v.x, v.y);
+            if (gz[i] >= 0 && (v.x != 0.f || v.y != 0.f))
+                atomic_add_cplx(grid + ((int64_t)gz[i] * a.n1 + g) * a.n0, v.x, v.y);
         }
     };
     auto step = [&](int i) {
@@ -941,77 +941,88 @@ __device__ __forceinline__ void spread_planes3_sub(const KArgs<T> &a, int4 sub, 
         }
     };
 
+    // The records come ordered by start row (setpts), in runs of at most
+    // kRowPiece points.  row is the oldest padded row held (slot k, fine-grid
+    // row g); a point starting at row r needs rows r .. r + W - 1: the rows
+    // below r are complete and are flushed first; a point starting below row
+    // (the next run) or W or more rows above it flushes all W slots, and so does
+    // the end of the subproblem (one past the last point).
     const R *recs = a.recs + sub.y;
-    for (int piece = 0; piece < n; piece += kSweepCap) {
-        const int np = min(kSweepCap, n - piece);
-        sweep_row_order<T, 0>(recs + piece, np, a.m1 + 1, idx, cnt);
-        R rc;
-        C cv;
-        if (lane < np) {
-            rc = recs[piece + idx[lane]];
-            cv = cin[a.order[sub.y + piece + idx[lane]]];
+    const int32_t *ord = a.order + sub.y;
+    int row = 0, k = 0, g = grow0;
+    R rc;
+    C cv;
+    if (lane < n) {
+        rc = recs[lane];
+        cv = cin[ord[lane]];
+    }
+    for (int base = 0; base < n; base += 32) {
+        const int c = min(32, n - base);
+        int myrow = 0x7fffffff;
+        __syncwarp();                                      // the old slots are consumed
+        if (lane < c) {
+            const uint32_t pk = unpack_word<T>(rc.w);
+            float *s = stg + lane * SLOT;
+            const int sx = (int)(pk & 1023u);
+            const int sy = (int)((pk >> 10) & 1023u);
+            const int sz = (int)(pk >> 20);
+            myrow = sy;
+            float vx[W], vy[W], vz[W];
+            kernel_row<T, W>(a, rc.x, vx);
+            kernel_row<T, W>(a, rc.y, vy);
+            kernel_row<T, W>(a, rc.z, vz);
+#pragma unroll
+            for (int kk = 0; kk < 32; kk += 4) store_zero_quad(s + OCX + kk);
+#pragma unroll
+            for (int kk = 0; kk < 4 * KZ; kk += 4) store_zero_quad(s + OWZ + kk);
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) = make_float2(cv.x * vx[i], cv.y * vx[i]);
+                *reinterpret_cast<float2 *>(s + OWZ + 2 * (sz + i)) = make_float2(vz[i], vz[i]);
+            }
+            int slot = sy % W;                             // w_y[i] goes to slot (sy + i) mod W
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                *reinterpret_cast<float2 *>(s + 2 * slot) = make_float2(vy[i], vy[i]);
+                slot = slot + 1 == W ? 0 : slot + 1;
+            }
         }
-        int bbase = -32, bend = 0;                         // staged positions [bbase, bend)
-        auto stage_next = [&]() {
-            __syncwarp();                                  // the old slots are consumed
-            bbase += 32;
-            const int c = min(32, np - bbase);
-            if (lane < c) {
-                const uint32_t pk = unpack_word<T>(rc.w);
-                float *s = stg + lane * SLOT;
-                const int sx = (int)(pk & 1023u);
-                const int sy = (int)((pk >> 10) & 1023u);
-                const int sz = (int)(pk >> 20);
-                float vx[W], vy[W], vz[W];
-                kernel_row<T, W>(a, rc.x, vx);
-                kernel_row<T, W>(a, rc.y, vy);
-                kernel_row<T, W>(a, rc.z, vz);
-#pragma unroll
-                for (int k = 0; k < 32; k += 4) store_zero_quad(s + OCX + k);
-#pragma unroll
-                for (int k = 0; k < 4 * KZ; k += 4) store_zero_quad(s + OWZ + k);
-#pragma unroll
-                for (int i = 0; i < W; ++i) {
-                    *reinterpret_cast<C *>(s + OCX + 2 * (sx + i)) =
-                        make_float2(cv.x * vx[i], cv.y * vx[i]);
-                    *reinterpret_cast<float2 *>(s + OWZ + 2 * (sz + i)) = make_float2(vz[i], vz[i]);
-                }
-                int slot = sy % W;                         // w_y[k] goes to slot (sy + k) mod W
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    *reinterpret_cast<float2 *>(s + 2 * slot) = make_float2(vy[k], vy[k]);
-                    slot = slot + 1 == W ? 0 : slot + 1;
-                }
-            }
-            const int nb = bbase + 32;                     // prefetch the next batch
-            if (nb + lane < np) {
-                rc = recs[piece + idx[nb + lane]];
-                cv = cin[a.order[sub.y + piece + idx[nb + lane]]];
-            }
-            bend = bbase + c;
-            __syncwarp();
-        };
-        int pos = 0;
-        int g = grow0;
-        int k = 0;                                         // slot of row r = r mod W
-#pragma unroll 1
-        for (int r = 0; r < a.p1; ++r) {
-            const int end = r <= a.m1 ? cnt[r] : pos;
-            while (pos < end) {
-                if (pos == bend) stage_next();
-                const int e = min(end, bend);
-                const int ie = e - bbase;
-#pragma unroll 1
-                for (int i = pos - bbase; i < ie; ++i) step(i);
-                pos = e;
-            }
-#pragma unroll
-            for (int kk = 0; kk < W; ++kk)                 // row r is complete: flush slot k
-                if (kk == k) flush(kk, g);
-            g = g + 1 == a.n1 ? 0 : g + 1;
-            k = k + 1 == W ? 0 : k + 1;
+        if (base + 32 + lane < n) {                        // the next batch in flight
+            rc = recs[base + 32 + lane];
+            cv = cin[ord[base + 32 + lane]];
         }
-        __syncwarp();                                      // idx / cnt reused by the next piece
+        if (base == 0) {
+            row = __shfl_sync(kFullMask, myrow, 0);
+            k = row % W;
+            g = wrap_any(grow0 + row, a.n1);
+        }
+        __syncwarp();
+        const int iend = base + 32 >= n ? c + 1 : c;      // the last batch ends with a full flush
+#pragma unroll 1
+        for (int i = 0; i < iend; ++i) {
+            const int rs = __shfl_sync(kFullMask, myrow, i < c ? i : 0);
+            const int r = i < c ? rs : 0x7fffffff;
+            if (r != row) {
+                const bool all = r < row || r - row >= W;
+                const int nf = all ? W : r - row;
+#pragma unroll 1
+                for (int f = 0; f < nf; ++f) {             // rows row .. row + nf - 1 are complete
+#pragma unroll
+                    for (int kk = 0; kk < W; ++kk)
+                        if (kk == k) flush(kk, g);
+                    k = k + 1 == W ? 0 : k + 1;
+                    g = g + 1 == a.n1 ? 0 : g + 1;
+                }
+                if (i < c) {
+                    if (all) {
+                        k = r % W;
+                        g = wrap_any(grow0 + r, a.n1);
+                    }
+                    row = r;
+                }
+            }
+            if (i < c) step(i);
+        }
     }
 }
 
@@ -1352,7 +1363,8 @@ template <int W, int M2> __host__ __device__ constexpr int iplanes3_slot()
 template <int W, int M2>
 __host__ __device__ inline size_t iplanes3_bytes(int m1)
 {
-    return sweep_head(m1 + 1) + sizeof(float) * (size_t)32 * iplanes3_slot<W, M2>();
+    (void)m1;
+    return sizeof(float) * (size_t)32 * iplanes3_slot<W, M2>();
 }
 
 template <typename T, int W, int M2>
@@ -1368,9 +1380,7 @@ __device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, 
     constexpr int OWZ = iplanes3_owz<W, M2>(), OWX = iplanes3_owx<W, M2>();
     const int lane = threadIdx.x & 31, h = lane >> 4, q = lane & 15;
     const int n = sub.z;
-    uint16_t *idx = reinterpret_cast<uint16_t *>(sm);
-    int *cnt = reinterpret_cast<int *>(sm + 2 * kSweepCap);
-    float *stg = reinterpret_cast<float *>(sm + sweep_head(a.m1 + 1));
+    float *stg = reinterpret_cast<float *>(sm);
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
     const int P = pad_lo(W);
@@ -1379,87 +1389,115 @@ __device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, 
     const bool xok = q < a.p0;
     const int gx = wrap_any(o0 - P + (xok ? q : 0), a.n0);
     const int grow0 = wrap_any(o1 - P, a.n1);
-    const C *col[KZ];                                      // (plane, column) of each owned cell
-    bool cok[KZ];
+    const C *gcol = grid + gx;
+    int gz[KZ];                                            // fine-grid plane of each owned plane
 #pragma unroll
-    for (int i = 0; i < KZ; ++i) {
-        cok[i] = xok && h * KZ + i < PZ;
-        col[i] = grid + (int64_t)wrap_any(o2 - P + h * KZ + i, a.n2) * a.n1 * a.n0 + gx;
-    }
-    auto load_row = [&](int g, float2 (&dst)[KZ]) {
+    for (int i = 0; i < KZ; ++i)
+        gz[i] = xok && h * KZ + i < PZ ? wrap_any(o2 - P + h * KZ + i, a.n2) : -1;
+    // padded row rr (fine-grid row gg) of every owned plane, zero past the padded bin
+    auto load_row = [&](int rr, int gg, float2 (&dst)[KZ]) {
 #pragma unroll
         for (int i = 0; i < KZ; ++i)
-            dst[i] = cok[i] ? __ldg(col[i] + (int64_t)g * a.n0) : make_float2(0.f, 0.f);
+            dst[i] = gz[i] >= 0 && rr < a.p1 ? __ldg(gcol + ((int64_t)gz[i] * a.n1 + gg) * a.n0)
+                                             : make_float2(0.f, 0.f);
     };
-    float2 g[KZ][W];                                       // g[i][slot]
-    float2 nxt[KZ];
+    float2 g[KZ][W];                                       // g[i][slot]: padded row = slot mod W
+    float2 nxt[KZ];                                        // row + W, in flight
+    auto put_slot = [&](int k, const float2 (&v)[KZ]) {
+#pragma unroll
+        for (int kk = 0; kk < W; ++kk)
+            if (kk == k) {
+#pragma unroll
+                for (int i = 0; i < KZ; ++i) g[i][kk] = v[i];
+            }
+    };
+    // rows r .. r + W - 1 into their slots, row r + W in flight
+    auto load_window = [&](int r) {
+        int gg = wrap_any(grow0 + r, a.n1);
+        int k = r % W;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            float2 v[KZ];
+            load_row(r + j, gg, v);
+            put_slot(k, v);
+            k = k + 1 == W ? 0 : k + 1;
+            gg = gg + 1 == a.n1 ? 0 : gg + 1;
+        }
+        load_row(r + W, gg, nxt);
+    };
 
+    // Records ordered by start row (setpts), in runs; row is the lowest padded
+    // row held.  Moving up one row puts the row in flight into the freed slot
+    // and starts the load of the next; any other change of row (the next run,
+    // or a gap) reloads the whole window.
     const R *recs = a.recs + sub.y;
-    for (int piece = 0; piece < n; piece += kSweepCap) {
-        const int np = min(kSweepCap, n - piece);
-        sweep_row_order<T, 0>(recs + piece, np, a.m1 + 1, idx, cnt);
-        // rows 0 .. W-1 into their slots, row W in flight
-        {
-            int gy = grow0;
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                float2 v[KZ];
-                load_row(gy, v);
-#pragma unroll
-                for (int i = 0; i < KZ; ++i) g[i][k] = v[i];
-                gy = gy + 1 == a.n1 ? 0 : gy + 1;
-            }
-            load_row(gy, nxt);
-        }
-        R rc;
-        int jn = 0;
-        if (lane < np) {
-            rc = recs[piece + idx[lane]];
-            jn = a.order[sub.y + piece + idx[lane]];
-        }
-        int bbase = -32, bend = 0, jout = 0;
+    const int32_t *ord = a.order + sub.y;
+    int row = 0, k = 0, gnext = 0;                         // gnext: fine-grid row of nxt
+    R rc;
+    int jn = 0;
+    if (lane < n) {
+        rc = recs[lane];
+        jn = ord[lane];
+    }
+    for (int base = 0; base < n; base += 32) {
+        const int c = min(32, n - base);
+        int myrow = 0x7fffffff, jout = 0;
         float2 res = make_float2(0.f, 0.f);
-        auto stage_next = [&]() {
-            __syncwarp();
-            if (bbase >= 0 && bbase + lane < bend) cout[jout] = res;   // the finished batch
-            bbase += 32;
-            const int c = min(32, np - bbase);
-            if (lane < c) {
-                const uint32_t pk = unpack_word<T>(rc.w);
-                float *s = stg + lane * SLOT;
-                const int sx = (int)(pk & 1023u);
-                const int sy = (int)((pk >> 10) & 1023u);
-                const int sz = (int)(pk >> 20);
-                float vx[W], vy[W], vz[W];
-                kernel_row<T, W>(a, rc.x, vx);
-                kernel_row<T, W>(a, rc.y, vy);
-                kernel_row<T, W>(a, rc.z, vz);
+        __syncwarp();
+        if (lane < c) {
+            const uint32_t pk = unpack_word<T>(rc.w);
+            float *s = stg + lane * SLOT;
+            const int sx = (int)(pk & 1023u);
+            const int sy = (int)((pk >> 10) & 1023u);
+            const int sz = (int)(pk >> 20);
+            myrow = sy;
+            jout = jn;
+            float vx[W], vy[W], vz[W];
+            kernel_row<T, W>(a, rc.x, vx);
+            kernel_row<T, W>(a, rc.y, vy);
+            kernel_row<T, W>(a, rc.z, vz);
 #pragma unroll
-                for (int k = 0; k < 16; k += 4) store_zero_quad(s + OWX + k);
+            for (int kk = 0; kk < 16; kk += 4) store_zero_quad(s + OWX + kk);
 #pragma unroll
-                for (int k = 0; k < OWX - OWZ; k += 4) store_zero_quad(s + OWZ + k);
+            for (int kk = 0; kk < OWX - OWZ; kk += 4) store_zero_quad(s + OWZ + kk);
 #pragma unroll
-                for (int i = 0; i < W; ++i) {
-                    s[OWX + sx + i] = vx[i];
-                    s[OWZ + sz + i] = vz[i];
-                }
-                int slot = sy % W;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    *reinterpret_cast<float2 *>(s + 2 * slot) = make_float2(vy[k], vy[k]);
-                    slot = slot + 1 == W ? 0 : slot + 1;
-                }
-                jout = jn;
+            for (int i = 0; i < W; ++i) {
+                s[OWX + sx + i] = vx[i];
+                s[OWZ + sz + i] = vz[i];
             }
-            const int nb = bbase + 32;
-            if (nb + lane < np) {
-                rc = recs[piece + idx[nb + lane]];
-                jn = a.order[sub.y + piece + idx[nb + lane]];
+            int slot = sy % W;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                *reinterpret_cast<float2 *>(s + 2 * slot) = make_float2(vy[i], vy[i]);
+                slot = slot + 1 == W ? 0 : slot + 1;
             }
-            bend = bbase + c;
-            __syncwarp();
-        };
-        auto step = [&](int i) {
+        }
+        if (base + 32 + lane < n) {
+            rc = recs[base + 32 + lane];
+            jn = ord[base + 32 + lane];
+        }
+        if (base == 0) {
+            row = __shfl_sync(kFullMask, myrow, 0);
+            k = row % W;
+            load_window(row);
+            gnext = wrap_any(grow0 + row + W, a.n1);
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int i = 0; i < c; ++i) {
+            const int r = __shfl_sync(kFullMask, myrow, i);
+            if (r == row + 1) {                            // slot k (row) takes row + W
+                put_slot(k, nxt);
+                k = k + 1 == W ? 0 : k + 1;
+                gnext = gnext + 1 == a.n1 ? 0 : gnext + 1;
+                row = r;
+                load_row(row + W, gnext, nxt);
+            } else if (r != row) {                         // a new run or a jump
+                row = r;
+                k = r % W;
+                load_window(r);
+                gnext = wrap_any(grow0 + r + W, a.n1);
+            }
             const float *s = stg + i * SLOT;
             const float wx = s[OWX + q];
             float wz[KZ];
@@ -1485,55 +1523,28 @@ __device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, 
             }
             float2 u[KZ];
 #pragma unroll
-            for (int k = 0; k < W; k += 2) {
-                const float4 wp = *reinterpret_cast<const float4 *>(s + 2 * k);
+            for (int kk = 0; kk < W; kk += 2) {
+                const float4 wp = *reinterpret_cast<const float4 *>(s + 2 * kk);
 #pragma unroll
                 for (int j = 0; j < KZ; ++j) {
-                    if (k == 0) u[j] = mul2(g[j][0], make_float2(wp.x, wp.y));
-                    else fma2(u[j], g[j][k], make_float2(wp.x, wp.y));
-                    if (k + 1 < W) fma2(u[j], g[j][k + 1 < W ? k + 1 : k], make_float2(wp.z, wp.w));
+                    if (kk == 0) u[j] = mul2(g[j][0], make_float2(wp.x, wp.y));
+                    else fma2(u[j], g[j][kk], make_float2(wp.x, wp.y));
+                    if (kk + 1 < W) fma2(u[j], g[j][kk + 1 < W ? kk + 1 : kk], make_float2(wp.z, wp.w));
                 }
             }
             float2 v = make_float2(0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < KZ; ++j) {
-                const float t = wx * wz[j];
-                fma2(v, u[j], make_float2(t, t));
+                const float tw = wx * wz[j];
+                fma2(v, u[j], make_float2(tw, tw));
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 v = __fadd2_rn(v, make_float2(__shfl_xor_sync(kFullMask, v.x, o),
                                               __shfl_xor_sync(kFullMask, v.y, o)));
             if (lane == i) res = v;
-        };
-        int pos = 0;
-        int gy = grow0 + W < a.n1 ? grow0 + W : (grow0 + W) % a.n1;   // row of nxt
-        int k = 0;                                         // slot of row r
-#pragma unroll 1
-        for (int r = 0; r <= a.m1; ++r) {
-            const int end = cnt[r];
-            while (pos < end) {
-                if (pos == bend) stage_next();
-                const int e = min(end, bend);
-                const int ie = e - bbase;
-#pragma unroll 1
-                for (int i = pos - bbase; i < ie; ++i) step(i);
-                pos = e;
-            }
-            // row r is no longer read: its slot takes row r + W, the next row loads
-#pragma unroll
-            for (int kk = 0; kk < W; ++kk)
-                if (kk == k) {
-#pragma unroll
-                    for (int i = 0; i < KZ; ++i) g[i][kk] = nxt[i];
-                }
-            gy = gy + 1 == a.n1 ? 0 : gy + 1;
-            if (r + W + 1 < a.p1) load_row(gy, nxt);
-            k = k + 1 == W ? 0 : k + 1;
         }
-        __syncwarp();
-        if (bbase >= 0 && bbase + lane < bend) cout[jout] = res;
-        __syncwarp();                                      // idx / cnt reused by the next piece
+        if (lane < c) cout[jout] = res;                    // this batch's values
     }
 }
 
@@ -2000,7 +2011,9 @@ KArgs<T> make_args(const Plan &p)
 {
     KArgs<T> a;
     a.recs = reinterpret_cast<const typename rec4<T>::type *>(p.recs);
-    a.order = p.perm;                              // records are in t order
+    // index of the point at each record position: t, or its copy reordered with
+    // the records by start row (3D plane-split plans)
+    a.order = p.row_ordered ? p.rorder : p.perm;
     a.subprob = p.subprob;
     a.nsub = p.nsub;
     a.xyz0 = reinterpret_cast<const T *>(p.xyz_copy[0]);

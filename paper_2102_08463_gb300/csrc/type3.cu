@@ -356,6 +356,7 @@ int t3_execute(Plan &p, const void *c, void *f)
     Type3 &t = *p.t3;
     using C = typename cplx<T>::type;
     const int nt = p.ntransf;
+    if ((t.K > 0 && !f) || (t.K > 0 && t.M > 0 && !c)) return NUFFT_ERR_ARG;
     if (t.K == 0) return NUFFT_OK;
     if (t.M == 0) {
         cudaError_t e = cudaMemsetAsync(f, 0, 2 * sizeof(T) * (size_t)t.K * nt, p.stream);
