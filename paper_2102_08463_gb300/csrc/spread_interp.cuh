@@ -997,23 +997,35 @@ __device__ __forceinline__ void spread_planes3_sub(const KArgs<T> &a, int4 sub, 
             g = wrap_any(grow0 + row, a.n1);
         }
         __syncwarp();
-        const int iend = base + 32 >= n ? c + 1 : c;      // the last batch ends with a full flush
-#pragma unroll 1
-        for (int i = 0; i < iend; ++i) {
-            const int rs = __shfl_sync(kFullMask, myrow, i < c ? i : 0);
-            const int r = i < c ? rs : 0x7fffffff;
+        // the batch as segments of equal start row: one ballot, then per segment
+        // the rows below it are flushed and its points run back to back
+        const int prev = __shfl_up_sync(kFullMask, myrow, 1);
+        unsigned starts = __ballot_sync(kFullMask, lane < c && (lane == 0 || myrow != prev));
+        const bool last = base + 32 >= n;
+        while (starts != 0u || last) {
+            const int i0 = starts ? __ffs(starts) - 1 : c;     // c: the end of the subproblem
+            if (starts) starts &= starts - 1;
+            const int i1 = starts ? __ffs(starts) - 1 : c;
+            const int r = i0 < c ? __shfl_sync(kFullMask, myrow, i0) : 0x7fffffff;
             if (r != row) {
                 const bool all = r < row || r - row >= W;
                 const int nf = all ? W : r - row;
 #pragma unroll 1
                 for (int f = 0; f < nf; ++f) {             // rows row .. row + nf - 1 are complete
-#pragma unroll
-                    for (int kk = 0; kk < W; ++kk)
-                        if (kk == k) flush(kk, g);
+                    switch (k) {                           // W <= 8 slots
+                    case 0: flush(0, g); break;
+                    case 1: if constexpr (W > 1) flush(1, g); break;
+                    case 2: if constexpr (W > 2) flush(2, g); break;
+                    case 3: if constexpr (W > 3) flush(3, g); break;
+                    case 4: if constexpr (W > 4) flush(4, g); break;
+                    case 5: if constexpr (W > 5) flush(5, g); break;
+                    case 6: if constexpr (W > 6) flush(6, g); break;
+                    default: if constexpr (W > 7) flush(7, g); break;
+                    }
                     k = k + 1 == W ? 0 : k + 1;
                     g = g + 1 == a.n1 ? 0 : g + 1;
                 }
-                if (i < c) {
+                if (i0 < c) {
                     if (all) {
                         k = r % W;
                         g = wrap_any(grow0 + r, a.n1);
@@ -1021,7 +1033,9 @@ __device__ __forceinline__ void spread_planes3_sub(const KArgs<T> &a, int4 sub, 
                     row = r;
                 }
             }
-            if (i < c) step(i);
+            if (i0 >= c) break;
+#pragma unroll 1
+            for (int i = i0; i < i1; ++i) step(i);
         }
     }
 }
@@ -1483,66 +1497,73 @@ __device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, 
             gnext = wrap_any(grow0 + row + W, a.n1);
         }
         __syncwarp();
-#pragma unroll 1
-        for (int i = 0; i < c; ++i) {
-            const int r = __shfl_sync(kFullMask, myrow, i);
+        const int prev = __shfl_up_sync(kFullMask, myrow, 1);
+        unsigned starts = __ballot_sync(kFullMask, lane < c && (lane == 0 || myrow != prev));
+        while (starts) {                                   // segments of equal start row
+            const int i0 = __ffs(starts) - 1;
+            starts &= starts - 1;
+            const int i1 = starts ? __ffs(starts) - 1 : c;
+            const int r = __shfl_sync(kFullMask, myrow, i0);
             if (r == row + 1) {                            // slot k (row) takes row + W
                 put_slot(k, nxt);
                 k = k + 1 == W ? 0 : k + 1;
                 gnext = gnext + 1 == a.n1 ? 0 : gnext + 1;
                 row = r;
                 load_row(row + W, gnext, nxt);
-            } else if (r != row) {                         // a new run or a jump
+            } else if (r != row) {                         // a new run or a gap
                 row = r;
                 k = r % W;
                 load_window(r);
                 gnext = wrap_any(grow0 + r + W, a.n1);
             }
-            const float *s = stg + i * SLOT;
-            const float wx = s[OWX + q];
-            float wz[KZ];
-            if constexpr (KZ % 4 == 0) {
+#pragma unroll 1
+            for (int i = i0; i < i1; ++i) {
+                const float *s = stg + i * SLOT;
+                const float wx = s[OWX + q];
+                float wz[KZ];
+                if constexpr (KZ % 4 == 0) {
 #pragma unroll
-                for (int j = 0; j < KZ; j += 4) {
-                    const float4 z4 = *reinterpret_cast<const float4 *>(s + OWZ + h * KZ + j);
-                    wz[j] = z4.x;
-                    wz[j + 1] = z4.y;
-                    wz[j + 2] = z4.z;
-                    wz[j + 3] = z4.w;
+                    for (int j = 0; j < KZ; j += 4) {
+                        const float4 z4 = *reinterpret_cast<const float4 *>(s + OWZ + h * KZ + j);
+                        wz[j] = z4.x;
+                        wz[j + 1] = z4.y;
+                        wz[j + 2] = z4.z;
+                        wz[j + 3] = z4.w;
+                    }
+                } else if constexpr (KZ % 2 == 0) {
+#pragma unroll
+                    for (int j = 0; j < KZ; j += 2) {
+                        const float2 z2 = *reinterpret_cast<const float2 *>(s + OWZ + h * KZ + j);
+                        wz[j] = z2.x;
+                        wz[j + 1 < KZ ? j + 1 : j] = z2.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < KZ; ++j) wz[j] = s[OWZ + h * KZ + j];
                 }
-            } else if constexpr (KZ % 2 == 0) {
+                float2 u[KZ];
 #pragma unroll
-                for (int j = 0; j < KZ; j += 2) {
-                    const float2 z2 = *reinterpret_cast<const float2 *>(s + OWZ + h * KZ + j);
-                    wz[j] = z2.x;
-                    wz[j + 1 < KZ ? j + 1 : j] = z2.y;
+                for (int kk = 0; kk < W; kk += 2) {
+                    const float4 wp = *reinterpret_cast<const float4 *>(s + 2 * kk);
+#pragma unroll
+                    for (int j = 0; j < KZ; ++j) {
+                        if (kk == 0) u[j] = mul2(g[j][0], make_float2(wp.x, wp.y));
+                        else fma2(u[j], g[j][kk], make_float2(wp.x, wp.y));
+                        if (kk + 1 < W) fma2(u[j], g[j][kk + 1 < W ? kk + 1 : kk], make_float2(wp.z, wp.w));
+                    }
                 }
-            } else {
-#pragma unroll
-                for (int j = 0; j < KZ; ++j) wz[j] = s[OWZ + h * KZ + j];
-            }
-            float2 u[KZ];
-#pragma unroll
-            for (int kk = 0; kk < W; kk += 2) {
-                const float4 wp = *reinterpret_cast<const float4 *>(s + 2 * kk);
+                float2 v = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < KZ; ++j) {
-                    if (kk == 0) u[j] = mul2(g[j][0], make_float2(wp.x, wp.y));
-                    else fma2(u[j], g[j][kk], make_float2(wp.x, wp.y));
-                    if (kk + 1 < W) fma2(u[j], g[j][kk + 1 < W ? kk + 1 : kk], make_float2(wp.z, wp.w));
+                    const float tw = wx * wz[j];
+                    fma2(v, u[j], make_float2(tw, tw));
                 }
-            }
-            float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < KZ; ++j) {
-                const float tw = wx * wz[j];
-                fma2(v, u[j], make_float2(tw, tw));
+                for (int o = 16; o > 0; o >>= 1)
+                    v = __fadd2_rn(v, make_float2(__shfl_xor_sync(kFullMask, v.x, o),
+                                                  __shfl_xor_sync(kFullMask, v.y, o)));
+                if (lane == i) res = v;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                v = __fadd2_rn(v, make_float2(__shfl_xor_sync(kFullMask, v.x, o),
-                                              __shfl_xor_sync(kFullMask, v.y, o)));
-            if (lane == i) res = v;
         }
         if (lane < c) cout[jout] = res;                    // this batch's values
     }

@@ -454,7 +454,10 @@ def test_edge_coordinates(nb):
 
 def test_errors(nb):
     with pytest.raises(nb.NufftError) as e:
-        nb.makeplan(3, 2, (8, 8))
+        nb.makeplan(4, 2, (8, 8))                   # types 1, 2 and 3 only
+    assert e.value.code == nb.NUFFT_ERR_ARG
+    with pytest.raises(nb.NufftError) as e:
+        nb.makeplan(1, 0, (8, 8))                   # dimensions 1 to 3
     assert e.value.code == nb.NUFFT_ERR_ARG
     with pytest.raises(nb.NufftError) as e:
         nb.makeplan(1, 2, (8, 8), eps=1e-9, prec=0)

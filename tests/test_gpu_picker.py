@@ -236,3 +236,21 @@ def test_committed_picker_choices_are_accurate(nb):
     finally:
         nb.Picker.uninstall()
         pk.close()
+
+
+def test_trained_picker_gains_over_the_heuristic(nb):
+    # What the learned picker buys: trained with the library's kernels on the
+    # committed GB300 trials (training split), its choices on the held-out
+    # problems must total less execute time than the heuristic tiles -- using the
+    # measured times stored with every candidate, so nothing is re-timed here.
+    from paper_2102_08463_gb300 import picker as pk
+    rows = pk.load_rows(pk.DEFAULT_TRIALS)
+    held = [r for r in rows if pk.is_heldout(r["seed"])]
+    assert len(held) >= 30
+    p, loss = pk.train(rows, epochs=300, batch=256, lr=2e-3, seed=1)
+    assert loss < 0.2                      # MSE in log2(ms)
+    tot = pk.evaluate(p, rows)
+    assert tot["problems"] >= 30
+    assert tot["picker"] < 0.9 * tot["heuristic"], tot
+    assert tot["regret"] < 0.5, tot
+    p.close()
