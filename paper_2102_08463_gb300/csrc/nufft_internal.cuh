@@ -232,6 +232,7 @@ struct Plan {
     int32_t *rorder = nullptr;     // [Mcap] 3D: record position -> original index
     bool row_ordered = false;      // records ordered by start row inside each subproblem
     void *recs = nullptr;          // [Mcap] rec4<T> per point, in t order (see setpts.cu)
+    void *recs2 = nullptr;         // [Mcap] 3D: the other record buffer of the row ordering
     void *xyz_copy[3] = {nullptr, nullptr, nullptr};  // coordinate copies for GM
     int32_t *bincount = nullptr;   // [nbins]
     int32_t *binstart = nullptr;   // [nbins]
@@ -381,6 +382,9 @@ int sweep_variant(const Plan &p);
 // SM, w <= 8, padded width <= 16, m2 in {1, 2}), else 0; setpts orders such a
 // plan's records by start row and sweep_variant then reports the form.
 int planes3_form(const Plan &p);
+// 8, 16 or 32 (sub-warp lanes) if a 2D type 1 SM plan suits the spreading row
+// sweep (padded width <= 32), else 0.
+int sweep2_form(const Plan &p);
 cudaError_t spread_multi_f32_1d(const MultiLaunch &ml);
 cudaError_t spread_multi_f64_1d(const MultiLaunch &ml);
 cudaError_t interp_multi_f32_1d(const MultiLaunch &ml);

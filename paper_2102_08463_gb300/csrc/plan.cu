@@ -107,6 +107,8 @@ void free_points(Plan &p)
     dev_free(p.recs);
     dev_free(p.rorder);
     p.rorder = nullptr;
+    dev_free(p.recs2);
+    p.recs2 = nullptr;
     p.row_ordered = false;
     dev_free(p.subprob);
     for (int d = 0; d < 3; ++d) {
@@ -301,6 +303,7 @@ int nufft::sweep_variant(const Plan &p)
 {
     if (p.method != NUFFT_METHOD_SM) return 0;
     const int p0 = padded(p.m[0], p.w);
+    if (p.dim == 2 && p.type == 2) return 0;
     if (p.dim == 3) {
         // the plane-split sweeps read records ordered by start row (setpts)
         const int f = planes3_form(p);
@@ -308,8 +311,14 @@ int nufft::sweep_variant(const Plan &p)
         if (p.type == 2) return 0;
         return p0 <= 32 && p.prec == 0 && p.w <= 8 && (p.m[2] == 1 || p.m[2] == 2) ? p.m[2] : 0;
     }
-    if (p.type != 1 || p.dim != 2 || p0 > 32) return 0;
-    return p0 <= 8 ? 8 : (p0 <= 16 ? 16 : 32);
+    return sweep2_form(p);
+}
+
+int nufft::sweep2_form(const Plan &p)
+{
+    if (p.method != NUFFT_METHOD_SM || p.dim != 2 || p.type != 1) return 0;
+    const int p0 = padded(p.m[0], p.w);
+    return p0 <= 8 ? 8 : (p0 <= 16 ? 16 : (p0 <= 32 ? 32 : 0));
 }
 
 bool nufft::tiles_feasible(const Plan &p, const Tiles &t)
@@ -641,6 +650,7 @@ int nufft_setpts(nufft_plan h, int64_t M, const void *x, const void *y, const vo
         if (rc == NUFFT_OK) rc = dev_alloc(&p.vals_alt, sizeof(int32_t) * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.recs, rsz * cap);
         if (rc == NUFFT_OK && p.dim == 3) rc = dev_alloc(&p.rorder, sizeof(int32_t) * cap);
+        if (rc == NUFFT_OK && p.dim == 3) rc = dev_alloc(&p.recs2, rsz * cap);
         if (rc == NUFFT_OK) rc = dev_alloc(&p.subprob, sizeof(int4) * maxsub);
         if (rc != NUFFT_OK) {
             free_points(p);

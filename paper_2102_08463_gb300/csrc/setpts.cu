@@ -459,6 +459,75 @@ records_from_perm_kernel(const int32_t *__restrict__ perm, int64_t M, const T *_
     }
 }
 
+// 3D plane-split sweeps: the records of every subproblem put in order of window
+// start row (stable: t order inside a row), out of place from the t-ordered
+// records into the plan's second record buffer, with the point indices moved
+// alike into rorder.  One warp per subproblem: the start rows are counted
+// (warp-aggregated shared atomics), prefix-summed, and every record is copied to
+// its position.  The records are read in order (coalesced) twice; t itself is
+// not touched.
+constexpr int kRowWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kRowWarps * 32)
+row_order_kernel(const typename rec4<T>::type *__restrict__ recs_in,
+                 const int32_t *__restrict__ perm, const int4 *__restrict__ subprob,
+                 const int32_t *__restrict__ nsub, int nkeys,
+                 typename rec4<T>::type *__restrict__ recs_out, int32_t *__restrict__ rorder)
+{
+    extern __shared__ int cnt_all[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int *cnt = cnt_all + warp * (nkeys + 1);
+    const unsigned lt = (1u << lane) - 1u;
+    const int ns = *nsub;
+    for (int sp = blockIdx.x * kRowWarps + warp; sp < ns; sp += gridDim.x * kRowWarps) {
+        const int4 sub = subprob[sp];
+        const typename rec4<T>::type *in = recs_in + sub.y;
+        for (int i = lane; i <= nkeys; i += 32) cnt[i] = 0;
+        __syncwarp();
+        for (int b = 0; b < sub.z; b += 32) {
+            const int i = b + lane;
+            const int key = i < sub.z ? (int)((unpack_word_t<T>(in[i].w) >> 10) & 1023u) : 0x7fffffff;
+            const unsigned peers = __match_any_sync(kFull, key);
+            if (i < sub.z && (peers & lt) == 0) atomicAdd(&cnt[key + 1], __popc(peers));
+        }
+        __syncwarp();
+        int running = 0;
+        for (int i0 = 0; i0 <= nkeys; i0 += 32) {
+            const int i = i0 + lane;
+            int v = i <= nkeys ? cnt[i] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, v, o);
+                if (lane >= o) v += t;
+            }
+            if (i <= nkeys) cnt[i] = running + v;
+            running += __shfl_sync(kFull, v, 31);
+        }
+        __syncwarp();
+        for (int b = 0; b < sub.z; b += 32) {
+            const int i = b + lane;
+            typename rec4<T>::type r;
+            int key = 0x7fffffff, j = 0;
+            if (i < sub.z) {
+                r = in[i];
+                j = perm[sub.y + i];
+                key = (int)((unpack_word_t<T>(r.w) >> 10) & 1023u);
+            }
+            const unsigned peers = __match_any_sync(kFull, key);
+            const int leader = __ffs(peers) - 1;
+            int pos = 0;
+            if (i < sub.z && lane == leader) pos = atomicAdd(&cnt[key], __popc(peers));
+            pos = __shfl_sync(kFull, pos, leader) + __popc(peers & lt);
+            if (i < sub.z) {
+                recs_out[sub.y + pos] = r;
+                rorder[sub.y + pos] = j;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // LSD radix path (bins too many for shared memory).
 // ---------------------------------------------------------------------------
@@ -704,105 +773,33 @@ cudaError_t launch_records(Plan &p, const T *x, const T *y, const T *z,
     return cudaGetLastError();
 }
 
-// 3D plane-split sweeps: inside every subproblem the records are put in order
-// of window start row (stable, in pieces of kRowPiece points), with the point
-// indices moved alike into rorder.  The sweeps then read each subproblem as
-// runs of ascending start rows and need no ordering of their own; t itself is
-// unchanged (rorder is a copy reordered with the records).
-constexpr int kRowPiece = 1024;
-constexpr int kRowWarps = 4;
-
-template <typename T>
-__global__ void __launch_bounds__(kRowWarps * 32)
-row_order_kernel(typename rec4<T>::type *__restrict__ recs, const int32_t *__restrict__ perm,
-                 const int4 *__restrict__ subprob, const int32_t *__restrict__ nsub, int nkeys,
-                 int32_t *__restrict__ rorder)
-{
-    using R = typename rec4<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)kRowPiece * (sizeof(R) + 4) + 4 * (nkeys + 1);
-    unsigned char *base = smem_raw + warp * ((per_warp + 15) & ~(size_t)15);
-    R *srec = reinterpret_cast<R *>(base);
-    int32_t *sidx = reinterpret_cast<int32_t *>(base + kRowPiece * sizeof(R));
-    int *cnt = reinterpret_cast<int *>(base + (size_t)kRowPiece * (sizeof(R) + 4));
-    const unsigned lt = (1u << lane) - 1u;
-    const int ns = *nsub;
-    for (int sp = blockIdx.x * kRowWarps + warp; sp < ns; sp += gridDim.x * kRowWarps) {
-        const int4 sub = subprob[sp];
-        for (int piece = 0; piece < sub.z; piece += kRowPiece) {
-            const int np = min(kRowPiece, sub.z - piece);
-            const int64_t b0 = (int64_t)sub.y + piece;
-            for (int i = lane; i <= nkeys; i += 32) cnt[i] = 0;
-            for (int i = lane; i < np; i += 32) {
-                srec[i] = recs[b0 + i];
-                sidx[i] = perm[b0 + i];
-            }
-            __syncwarp();
-            // counts per start row (warp-aggregated), exclusive prefix, stable scatter
-            for (int i0 = 0; i0 < np; i0 += 32) {
-                const int i = i0 + lane;
-                const int key = i < np ? (int)((unpack_word_t<T>(srec[i].w) >> 10) & 1023u) : 0x7fffffff;
-                const unsigned peers = __match_any_sync(kFull, key);
-                if (i < np && (peers & lt) == 0) atomicAdd(&cnt[key + 1], __popc(peers));
-            }
-            __syncwarp();
-            int running = 0;
-            for (int i0 = 0; i0 <= nkeys; i0 += 32) {
-                const int i = i0 + lane;
-                int v = i <= nkeys ? cnt[i] : 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(kFull, v, o);
-                    if (lane >= o) v += t;
-                }
-                if (i <= nkeys) cnt[i] = running + v;
-                running += __shfl_sync(kFull, v, 31);
-            }
-            __syncwarp();
-            for (int i0 = 0; i0 < np; i0 += 32) {
-                const int i = i0 + lane;
-                const int key = i < np ? (int)((unpack_word_t<T>(srec[i].w) >> 10) & 1023u) : 0x7fffffff;
-                const unsigned peers = __match_any_sync(kFull, key);
-                const int leader = __ffs(peers) - 1;
-                int pos = 0;
-                if (i < np && lane == leader) pos = atomicAdd(&cnt[key], __popc(peers));
-                pos = __shfl_sync(kFull, pos, leader) + __popc(peers & lt);
-                if (i < np) {
-                    recs[b0 + pos] = srec[i];
-                    rorder[b0 + pos] = sidx[i];
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-// Records (t order), then, for plans swept by the 3D plane-split kernels, their
-// order by start row inside each subproblem.
+// Records in t order; for the 3D plane-split sweeps then ordered by start row
+// inside every subproblem (row_order_kernel, into the second record buffer,
+// which becomes the plan's records).
 template <typename T>
 cudaError_t finish_records(Plan &p, const T *x, const T *y, const T *z,
                            typename rec4<T>::type *recs)
 {
-    cudaError_t e = launch_records<T>(p, x, y, z, recs);
     p.row_ordered = false;
-    if (e != cudaSuccess || p.dim != 3 || sizeof(T) != 4) return e;
-    if (planes3_form(p) == 0) return e;
-    using R = typename rec4<T>::type;
+    cudaError_t e = launch_records<T>(p, x, y, z, recs);
+    if (e != cudaSuccess || p.dim != 3 || sizeof(T) != 4 || planes3_form(p) == 0) return e;
     const int nkeys = p.m[1] + 1;
-    const size_t per_warp = (((size_t)kRowPiece * (sizeof(R) + 4) + 4 * (nkeys + 1)) + 15) & ~(size_t)15;
-    const size_t smem = per_warp * kRowWarps;
+    const size_t smem = sizeof(int) * (size_t)(nkeys + 1) * kRowWarps;
     auto k = row_order_kernel<T>;
-    e = allow_max_smem((const void *)k);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRowWarps * 32, smem);
     const int grid = p.num_sms * (per_sm < 1 ? 1 : per_sm);
+    auto *out = reinterpret_cast<typename rec4<T>::type *>(p.recs2);
     count_launch();
-    k<<<grid, kRowWarps * 32, smem, p.stream>>>(recs, p.perm, p.subprob, p.nsub, nkeys, p.rorder);
+    k<<<grid, kRowWarps * 32, smem, p.stream>>>(recs, p.perm, p.subprob, p.nsub, nkeys, out,
+                                                 p.rorder);
     e = cudaGetLastError();
-    if (e == cudaSuccess) p.row_ordered = true;
-    return e;
+    if (e != cudaSuccess) return e;
+    void *tmp = p.recs;                            // the ordered records become the plan's
+    p.recs = p.recs2;
+    p.recs2 = tmp;
+    p.row_ordered = true;
+    return cudaSuccess;
 }
 
 template <typename T>

@@ -941,12 +941,11 @@ __device__ __forceinline__ void spread_planes3_sub(const KArgs<T> &a, int4 sub, 
         }
     };
 
-    // The records come ordered by start row (setpts), in runs of at most
-    // kRowPiece points.  row is the oldest padded row held (slot k, fine-grid
-    // row g); a point starting at row r needs rows r .. r + W - 1: the rows
-    // below r are complete and are flushed first; a point starting below row
-    // (the next run) or W or more rows above it flushes all W slots, and so does
-    // the end of the subproblem (one past the last point).
+    // The records come ordered by start row (setpts).  row is the oldest padded
+    // row held (slot k, fine-grid row g); a point starting at row r needs rows
+    // r .. r + W - 1: the rows below r are complete and are flushed first; a row
+    // W or more above (or, defensively, below) the held ones flushes all W slots,
+    // and so does the end of the subproblem (one past the last point).
     const R *recs = a.recs + sub.y;
     const int32_t *ord = a.order + sub.y;
     int row = 0, k = 0, g = grow0;
@@ -1076,7 +1075,7 @@ __device__ __forceinline__ void spread_sweep2_item(const KArgs<T> &a, int sp, in
 }
 
 template <typename T, int W, int L>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 spread_sweep2_kernel(KArgs<T> a, int warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1440,8 +1439,7 @@ __device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, 
         load_row(r + W, gg, nxt);
     };
 
-    // Records ordered by start row (setpts), in runs; row is the lowest padded
-    // row held.  Moving up one row puts the row in flight into the freed slot
+    // Records ordered by start row (setpts); row is the lowest padded row held.  Moving up one row puts the row in flight into the freed slot
     // and starts the load of the next; any other change of row (the next run,
     // or a gap) reloads the whole window.
     const R *recs = a.recs + sub.y;

@@ -249,7 +249,7 @@ def test_trained_picker_gains_over_the_heuristic(nb):
     assert len(held) >= 30
     p, loss = pk.train(rows, epochs=300, batch=256, lr=2e-3, seed=1)
     assert loss < 0.2                      # MSE in log2(ms)
-    tot = pk.evaluate(p, rows)
+    tot, _ = pk.evaluate(p, rows)
     assert tot["problems"] >= 30
     assert tot["picker"] < 0.9 * tot["heuristic"], tot
     assert tot["regret"] < 0.5, tot
