@@ -74,10 +74,14 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_write.sum), keyed by kernel and workload, with the hash of the
 # kernel sources at capture time; a stale hash reports null.
 TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --metrics, bench command
-    # of profiles/launches_2d-1024-rand-eps1e-5.md with -k spread_sweep2|interp_warp2)
-    "spread:2d-1024-rand-eps1e-5:ef3412d7685dad33": 443805440,
-    "interp:2d-1024-rand-eps1e-5:ef3412d7685dad33": 298646272,
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --metrics ... -k
+    # regex:"spread_sweep2|interp_warp2" -c 2 on the bench command of
+    # profiles/launches_2d-1024-rand-eps1e-5.md; the 3D rows on --workload 3d-128-rand-eps1e-6
+    # with -k regex:"spread_sweep3|interp_planes3"; see profiles/traffic_2d-1024_3d-128.md)
+    "spread:2d-1024-rand-eps1e-5:d0e4e7dc9b9cc20f": 139997952 + 19410176,
+    "interp:2d-1024-rand-eps1e-5:d0e4e7dc9b9cc20f": 127090944 + 26018560,
+    "spread:3d-128-rand-eps1e-6:d0e4e7dc9b9cc20f": 1796869632 + 228108544,
+    "interp:3d-128-rand-eps1e-6:d0e4e7dc9b9cc20f": 994209792 + 507364096,
 }
 
 

@@ -764,6 +764,13 @@ class Plan3:
         execute(self.handle, _dptr(c, cd, "c"), _dptr(f, cd, "f"))
         return f
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def close(self):
         if self.handle:
             destroy(self.handle)
