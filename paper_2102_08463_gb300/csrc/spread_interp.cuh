@@ -1362,8 +1362,9 @@ __device__ __forceinline__ void interp_lane_item(const KArgs<T> &a, int sp, int 
 // PZ-wide row, both zero outside the window; w_y rotated to the row slots);
 // for each point every lane forms
 //   sum_i (w_x[q] w_z[h KZ + i]) sum_s g[i][s] w_y[s]
-// and a butterfly sum over the warp gives the point's value, kept by the lane
-// that staged it and stored once per batch.
+// and stores it in a per-batch table of partial sums (one row per point, pitch
+// 33); after the batch the lane that staged point i sums row i and stores the
+// point's value -- 2 operations per point instead of a 5-level butterfly.
 template <int W, int M2> __host__ __device__ constexpr int iplanes3_owz() { return 4 * ((W + 1) / 2); }
 template <int W, int M2> __host__ __device__ constexpr int iplanes3_owx()
 {
@@ -1377,7 +1378,8 @@ template <int W, int M2>
 __host__ __device__ inline size_t iplanes3_bytes(int m1)
 {
     (void)m1;
-    return sizeof(float) * (size_t)32 * iplanes3_slot<W, M2>();
+    // 32 staging slots, then the 32 x 33 partial sums of a batch (float2)
+    return sizeof(float) * (size_t)32 * iplanes3_slot<W, M2>() + sizeof(float2) * 32 * 33;
 }
 
 template <typename T, int W, int M2>
@@ -1394,6 +1396,7 @@ __device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, 
     const int lane = threadIdx.x & 31, h = lane >> 4, q = lane & 15;
     const int n = sub.z;
     float *stg = reinterpret_cast<float *>(sm);
+    float2 *part = reinterpret_cast<float2 *>(sm + sizeof(float) * 32 * SLOT);   // [point][lane], pitch 33
     int o0, o1, o2;
     bin_origin(sub.x, a.nb0, a.nb1, a.m0, a.m1, a.m2, o0, o1, o2);
     const int P = pad_lo(W);
@@ -1454,7 +1457,6 @@ __device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, 
     for (int base = 0; base < n; base += 32) {
         const int c = min(32, n - base);
         int myrow = 0x7fffffff, jout = 0;
-        float2 res = make_float2(0.f, 0.f);
         __syncwarp();
         if (lane < c) {
             const uint32_t pk = unpack_word<T>(rc.w);
@@ -1556,14 +1558,16 @@ __device__ __forceinline__ void interp_planes3_sub(const KArgs<T> &a, int4 sub, 
                     const float tw = wx * wz[j];
                     fma2(v, u[j], make_float2(tw, tw));
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    v = __fadd2_rn(v, make_float2(__shfl_xor_sync(kFullMask, v.x, o),
-                                                  __shfl_xor_sync(kFullMask, v.y, o)));
-                if (lane == i) res = v;
+                part[i * 33 + lane] = v;                   // summed over the lanes per batch
             }
         }
-        if (lane < c) cout[jout] = res;                    // this batch's values
+        __syncwarp();
+        if (lane < c) {                                    // lane i sums point i's 32 partials
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) acc = __fadd2_rn(acc, part[lane * 33 + l]);
+            cout[jout] = acc;
+        }
     }
 }
 
