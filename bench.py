@@ -78,10 +78,10 @@ TRAFFIC = {
     # regex:"spread_sweep2|interp_warp2" -c 2 on the bench command of
     # profiles/launches_2d-1024-rand-eps1e-5.md; the 3D rows on --workload 3d-128-rand-eps1e-6
     # with -k regex:"spread_sweep3|interp_planes3"; see profiles/traffic_2d-1024_3d-128.md)
-    "spread:2d-1024-rand-eps1e-5:d0e4e7dc9b9cc20f": 139997952 + 19410176,
-    "interp:2d-1024-rand-eps1e-5:d0e4e7dc9b9cc20f": 127090944 + 26018560,
-    "spread:3d-128-rand-eps1e-6:d0e4e7dc9b9cc20f": 1796869632 + 228108544,
-    "interp:3d-128-rand-eps1e-6:d0e4e7dc9b9cc20f": 994209792 + 507364096,
+    "spread:2d-1024-rand-eps1e-5:e4182cc8d343359e": 140114944 + 19632128,
+    "interp:2d-1024-rand-eps1e-5:e4182cc8d343359e": 126882560 + 25981440,
+    "spread:3d-128-rand-eps1e-6:e4182cc8d343359e": 1798426368 + 229019136,
+    "interp:3d-128-rand-eps1e-6:e4182cc8d343359e": 1070203904 + 506863872,
 }
 
 
