@@ -965,10 +965,12 @@ def run_picker_bench(args):
                 "mixture)",
         "config": {"workload": "picker-holdout: %d problems, 2D/3D, type 1/2, N_i in [32,1024], "
                                "M in [1e4,3e7], eps in [1e-12,1e-2] (work-bounded), every "
-                               "candidate tiling timed (median of 3 executes)" % tot["problems"],
+                               "candidate tiling at sigma 2 and (where it reaches eps) 1.25 "
+                               "timed (median of 3 executes)" % tot["problems"],
                    "weights": os.path.relpath(weights, ROOT)},
         "heuristic_ms": round(tot["heuristic"], 4), "best_ms": round(tot["best"], 4),
         "regret_vs_best": round(tot["regret"], 4),
+        "picked_sigma125": tot["picked_sigma125"],
         "speedup_vs_heuristic": round(tot["speedup_vs_heuristic"], 4),
         "collect_seconds": round(collect_s, 1),
         "per_problem": per,

@@ -405,6 +405,32 @@ int nufft_picker_features(int type, int dim, const int64_t *nmodes, double eps, 
 int nufft_point_skew(int dim, int prec, int64_t M, const void *x, const void *y, const void *z,
                      double *skew, void *stream);
 
+/* nufft_pick: the upsampling factor sigma and the tiles for a plan that is yet
+ * to be made, chosen by the installed picker from the points themselves.  The
+ * paper fixes sigma = 2 and names sigma = 1.25 as the choice that trades a
+ * wider kernel (more spreading work, Sec. 3) for a smaller fine grid (a cheaper
+ * FFT); sigma shapes the fine grid, the kernel and the cuFFT plan, so it is
+ * chosen here, before nufft_makeplan, not at setpts.
+ *   type, dim (2 or 3), nmodes, eps   as nufft_makeplan;
+ *   prec                0 or 1: the precision of x / y / z and of the plan to be
+ *                       made (sigma = 1.25 is a candidate in single precision
+ *                       only for eps >= 1e-4, as in makeplan);
+ *   M, x, y, z          the points (device arrays of prec; z NULL in 2D);
+ *   stream              the stream of the skew histogram and the prediction;
+ *   opts                in / out: on return upsampfac, method, bin[], msub and
+ *                       threads hold the candidate of least predicted execute
+ *                       time over sigma in {2, 1.25} and the autotuner's tile
+ *                       candidates; its other fields are left as given.  Pass it
+ *                       to nufft_makeplan unchanged.
+ * With no picker installed on this device: upsampfac = 2 (it reaches every eps
+ * that 1.25 reaches) and the tile fields automatic (0).  Synchronizes stream; the
+ * picker's scratch is shared as for plans with use_picker.
+ * Errors: NUFFT_ERR_ARG, NUFFT_ERR_SIZE, NUFFT_ERR_EPS (no sigma reaches eps at
+ * this precision), NUFFT_ERR_ALLOC, NUFFT_ERR_CUDA; opts is unchanged on an
+ * argument error. */
+int nufft_pick(int type, int dim, const int64_t *nmodes, double eps, int prec, int64_t M,
+               const void *x, const void *y, const void *z, void *stream, nufft_opts *opts);
+
 #ifdef __cplusplus
 }
 #endif

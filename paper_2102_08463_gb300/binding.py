@@ -41,7 +41,7 @@ EXPORTS = (
     "nufft_picker_load", "nufft_picker_predict", "nufft_picker_grad", "nufft_picker_step",
     "nufft_picker_train", "nufft_picker_loss", "nufft_picker_install", "nufft_picker_features",
     "nufft_point_skew", "nufft_fma_peak", "nufft_execute_host", "nufft_get_status",
-    "nufft_debug_fail", "nufft_setpts3",
+    "nufft_debug_fail", "nufft_setpts3", "nufft_pick",
 )
 
 PICKER_NFEAT = 12
@@ -157,6 +157,8 @@ def load():
                                               ctypes.c_double, I64, ctypes.c_double,
                                               ctypes.POINTER(Opts), FP]
         lib.nufft_point_skew.argtypes = [I, I, I64, P, P, P, ctypes.POINTER(ctypes.c_double), P]
+        lib.nufft_pick.argtypes = [I, I, ctypes.POINTER(I64), ctypes.c_double, I, I64, P, P, P, P,
+                                   ctypes.POINTER(Opts)]
         lib.nufft_fma_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double), P]
         lib.nufft_execute_host.argtypes = [P, I64, P, P, P, P, P]
         lib.nufft_get_status.argtypes = [P]
@@ -381,6 +383,25 @@ def point_skew(x, y, z=None, stream=None):
                                    ctypes.byref(s), ctypes.c_void_p(stream.cuda_stream)),
            "nufft_point_skew")
     return s.value
+
+
+def pick(type_, N, eps, x, y=None, z=None, stream=None):
+    """nufft_pick on torch tensors: the upsampling factor and tiles the installed
+    picker predicts fastest for these points, as Plan keyword arguments
+    (upsampfac, prec, method, bins, msub, threads); prec is the points' own."""
+    import torch
+    dim = len(N)
+    prec = 0 if x.dtype == torch.float32 else 1
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o = default_opts()
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in N] + [1] * (3 - dim)))
+    _check(load().nufft_pick(int(type_), dim, arr, float(eps), prec, int(x.shape[0]), _dptr(x),
+                             _dptr(y), _dptr(z), ctypes.c_void_p(stream.cuda_stream),
+                             ctypes.byref(o)), "nufft_pick")
+    inv = {v: k for k, v in METHODS.items()}
+    return dict(upsampfac=o.upsampfac, prec=prec, method=inv.get(o.method, o.method),
+                bins=tuple(o.bin[:dim]) if o.bin[0] > 0 else None, msub=o.msub, threads=o.threads)
 
 
 class Picker:

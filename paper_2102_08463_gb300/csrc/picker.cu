@@ -734,6 +734,98 @@ int nufft_picker_features(int type, int dim, const int64_t *nmodes, double eps, 
     return NUFFT_OK;
 }
 
+int nufft_pick(int type, int dim, const int64_t *nmodes, double eps, int prec, int64_t M,
+               const void *x, const void *y, const void *z, void *stream, nufft_opts *opts)
+{
+    if ((type != 1 && type != 2) || (dim != 2 && dim != 3) || !nmodes || !opts ||
+        !(eps > 0.0) || (prec != 0 && prec != 1) || M < 0)
+        return NUFFT_ERR_ARG;
+    if (M > 0 && (!x || !y || (dim == 3 && !z))) return NUFFT_ERR_ARG;
+    for (int d = 0; d < dim; ++d)
+        if (nmodes[d] < 1 || nmodes[d] > (1 << 26)) return NUFFT_ERR_SIZE;
+    // one light plan per upsampling factor whose plan at this precision reaches
+    // eps (the grid rule of makeplan); nothing is allocated
+    std::vector<Plan> grids;
+    for (double sigma : {2.0, 1.25}) {
+        const double fp32_floor = sigma == 2.0 ? 1e-6 : 1e-4;
+        if (prec == 0 && eps < fp32_floor) continue;
+        const int w = kernel_width(eps, sigma);
+        if (w > kMaxW) continue;
+        Plan q;
+        q.type = type;
+        q.dim = dim;
+        q.prec = prec;
+        q.eps = eps;
+        q.sigma = sigma;
+        q.w = w;
+        q.nftot = 1;
+        for (int d = 0; d < dim; ++d) {
+            q.N[d] = nmodes[d];
+            int64_t want = (int64_t)ceil(sigma * (double)nmodes[d] - 1e-9);
+            if (want < 2 * w) want = 2 * w;
+            q.nf[d] = next235(want);
+            q.nftot *= q.nf[d];
+        }
+        grids.push_back(q);
+    }
+    if (grids.empty()) return NUFFT_ERR_EPS;
+    // no picker: sigma = 2 (listed first; it reaches every eps 1.25 reaches), tiles automatic
+    opts->upsampfac = grids[0].sigma;
+    opts->method = NUFFT_METHOD_AUTO;
+    opts->bin[0] = opts->bin[1] = opts->bin[2] = 0;
+    opts->msub = 0;
+    opts->threads = 0;
+    std::lock_guard<std::mutex> lock(g_install_mutex);
+    nufft_picker h = g_installed;
+    if (!h) return NUFFT_OK;
+    int dev = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) return NUFFT_OK;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    for (Plan &q : grids) q.smem_optin = smem_optin;
+    const cudaStream_t st = (cudaStream_t)stream;
+    double skew = 0.0;
+    int rc = point_skew(dim, prec, M, x, y, z, h->hist, &skew, st);
+    if (rc != NUFFT_OK) return rc;
+    std::vector<int> gi;
+    std::vector<Tiles> cand;
+    for (size_t g = 0; g < grids.size(); ++g)
+        for (const Tiles &t : tile_candidates(grids[g]))
+            if (tiles_feasible(grids[g], t)) {
+                gi.push_back((int)g);
+                cand.push_back(t);
+            }
+    if (cand.empty()) return NUFFT_OK;
+    const int64_t nc = (int64_t)cand.size();
+    rc = grow(&h->feat, h->feat_cap, nc * (kFeat + 1));
+    if (rc != NUFFT_OK) return rc;
+    std::vector<float> X((size_t)nc * kFeat), yv((size_t)nc);
+    for (int64_t i = 0; i < nc; ++i) {
+        const Plan &q = grids[(size_t)gi[(size_t)i]];
+        features(type, dim, prec, q.w, (double)q.nftot, (double)M, skew, cand[(size_t)i],
+                 &X[(size_t)i * kFeat]);
+    }
+    cudaError_t e = cudaMemcpyAsync(h->feat, X.data(), sizeof(float) * X.size(),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return rc_of(e);
+    rc = predict(h, nc, h->feat, h->feat + nc * kFeat, st);
+    if (rc != NUFFT_OK) return rc;
+    e = cudaMemcpyAsync(yv.data(), h->feat + nc * kFeat, sizeof(float) * nc,
+                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return rc_of(e);
+    int64_t best = 0;
+    for (int64_t i = 1; i < nc; ++i)
+        if (yv[(size_t)i] < yv[(size_t)best]) best = i;
+    const Tiles &t = cand[(size_t)best];
+    opts->upsampfac = grids[(size_t)gi[(size_t)best]].sigma;
+    opts->method = t.method;
+    for (int d = 0; d < 3; ++d) opts->bin[d] = d < dim ? t.bin[d] : 0;
+    opts->msub = t.msub;
+    opts->threads = t.threads;
+    return NUFFT_OK;
+}
+
 int nufft_point_skew(int dim, int prec, int64_t M, const void *x, const void *y, const void *z,
                      double *skew, void *stream)
 {

@@ -10,11 +10,17 @@ log2(execute ms) of a problem under one candidate tiling; this module
   (sigma_g log-uniform in [0.01 pi, 0.5 pi]) or an 8-component Gaussian mixture,
   eps log-uniform in [1e-12, 1e-2], single precision for eps >= 1e-6; problems
   over a work bound are redrawn so that timing every candidate stays short;
-* times every candidate tiling of each problem with nufft_autotune (`collect`)
-  and stores one JSON line per problem;
+* times every candidate tiling of each problem with nufft_autotune, at the
+  upsampling factor sigma = 2 and, where the plan's precision reaches eps there,
+  at sigma = 1.25 (`collect`), and stores one JSON line per problem;
 * trains the perceptron on the 80 % of problems whose seed is not 0 mod 5
   (`train`), and compares, on the other 20 %, the execute time of the picker's
-  choice with the heuristic tiles and the fastest candidate (`evaluate`).
+  choice (over both factors) with the heuristic (sigma = 2, default tiles) and
+  the fastest candidate (`evaluate`).
+
+sigma needs no feature of its own: it enters through the kernel width w and the
+fine-grid size n_tot (features 3 and 4), the two quantities it trades against
+each other (spreading work ~ M w^d against FFT work ~ n_tot log n_tot).
 
 Usage:
     python -m paper_2102_08463_gb300.picker collect --count 200 --out trials.jsonl
@@ -74,12 +80,24 @@ def sample_problems(count: int, first_seed: int = 0, max_work: float = MAX_WORK,
         f = binding.picker_features(tp, N, eps, M, 0.0, "sm", prec=prec)
         w = int(round(f[3] * 16))
         nftot = 2.0 ** (f[4] * 32)
-        work = M * w ** dim * (16 if prec else 1)
+        w125 = sigma125_width(tp, N, eps, M, prec)
+        work = M * max(w, w125 or 0) ** dim * (16 if prec else 1)
         if work > max_work or nftot > max_nftot * 1.0001:
             continue
         out.append(dict(seed=seed, type=tp, dim=dim, N=list(N), M=M, kind=kind,
                         spread=spread, eps=eps, prec=prec, w=w))
     return out
+
+
+def sigma125_width(tp, N, eps, M, prec):
+    """Kernel width of the sigma = 1.25 plan at this precision, or None where that
+    plan does not reach eps (single precision below 1e-4, w over 16)."""
+    from . import binding
+    try:
+        f = binding.picker_features(tp, N, eps, M, 0.0, "sm", prec=prec, upsampfac=1.25)
+    except binding.NufftError:
+        return None
+    return int(round(f[3] * 16))
 
 
 def _inputs(pr, torch):
@@ -97,29 +115,43 @@ def _inputs(pr, torch):
     return pts, c, f
 
 
-def collect(problems, reps: int = 2, out=None, log=None):
-    """Time every candidate tiling of each problem; returns one dict per problem
-    (its fields, skew, heuristic tiles and trials) and appends JSON lines to out."""
+def collect(problems, reps: int = 2, out=None, log=None, seconds=None):
+    """Time every candidate tiling of each problem at sigma = 2 and, where it
+    reaches eps, sigma = 1.25; returns one dict per problem (its fields, skew,
+    heuristic tiles and trials [method, bin x3, M_sub, threads, sigma, ms]) and
+    appends JSON lines to out.  Stops after `seconds` of wall time if given."""
     import torch
     from . import binding
     rows = []
     fh = open(out, "a") if out else None
+    start = time.time()
     try:
         for i, pr in enumerate(problems):
+            if seconds is not None and time.time() - start > seconds:
+                break
             t0 = time.time()
             pts, c, f = _inputs(pr, torch)
             skew = binding.point_skew(*pts)
             with binding.Plan(pr["type"], pr["N"], pr["eps"], prec=pr["prec"]) as p:
                 heur = p.tiles()
-            best, best_ms, trials = binding.autotune(
-                pr["type"], pr["N"], pr["eps"], pr["M"], pts[0], pts[1],
-                pts[2] if pr["dim"] == 3 else None, c, f, prec=pr["prec"], reps=reps)
+            sigmas = [2.0]
+            if sigma125_width(pr["type"], pr["N"], pr["eps"], pr["M"], pr["prec"]):
+                sigmas.append(1.25)
+            rec, best_ms = [], float("inf")
+            for sg in sigmas:
+                base = binding.default_opts()
+                base.upsampfac = sg
+                _, ms, trials = binding.autotune(
+                    pr["type"], pr["N"], pr["eps"], pr["M"], pts[0], pts[1],
+                    pts[2] if pr["dim"] == 3 else None, c, f, prec=pr["prec"], reps=reps,
+                    base=base)
+                best_ms = min(best_ms, ms)
+                rec += [[t["method"]] + list(t["bin"]) + [t["msub"], t["threads"], sg,
+                                                          round(t["exec_ms"], 5)]
+                        for t in trials]
             binding.tune_cache_clear()
             row = dict(pr, skew=skew, heuristic=[heur["method"]] + list(heur["bin"]) +
-                       [heur["msub"], heur["threads"]],
-                       trials=[[t["method"]] + list(t["bin"]) + [t["msub"], t["threads"],
-                                                                 round(t["exec_ms"], 5)]
-                               for t in trials])
+                       [heur["msub"], heur["threads"]], trials=rec)
             rows.append(row)
             if fh:
                 fh.write(json.dumps(row) + "\n")
@@ -128,7 +160,7 @@ def collect(problems, reps: int = 2, out=None, log=None):
                 log("problem %d/%d seed %d: %dD type %d N=%s M=%d eps=%.1e %s -> best %.3f ms "
                     "(%d trials, %.1f s)" % (i + 1, len(problems), pr["seed"], pr["dim"],
                                              pr["type"], pr["N"], pr["M"], pr["eps"], pr["kind"],
-                                             best_ms, len(trials), time.time() - t0))
+                                             best_ms, len(rec), time.time() - t0))
             del pts, c, f
     finally:
         if fh:
@@ -141,15 +173,21 @@ def load_rows(path):
         return [json.loads(ln) for ln in fh if ln.strip()]
 
 
+def trial_sigma(t):
+    """Upsampling factor of a stored trial (rows without one were timed at 2)."""
+    return t[6] if len(t) == 8 else 2.0
+
+
 def features(row):
     """Feature matrix [n_trials, 12] and targets log2(ms) of one problem's trials."""
     from . import binding
     X, T = [], []
-    for m, b0, b1, b2, msub, th, ms in row["trials"]:
+    for t in row["trials"]:
+        m, b0, b1, b2, msub, th = t[:6]
         X.append(binding.picker_features(row["type"], row["N"], row["eps"], row["M"], row["skew"],
                                          m, bins=(b0, b1, b2)[:row["dim"]], msub=msub, threads=th,
-                                         prec=row["prec"]))
-        T.append(math.log2(max(ms, 1e-4)))
+                                         prec=row["prec"], upsampfac=trial_sigma(t)))
+        T.append(math.log2(max(t[-1], 1e-4)))
     return np.asarray(X, dtype=np.float32), np.asarray(T, dtype=np.float32)
 
 
@@ -184,15 +222,18 @@ def evaluate(picker, rows):
         pred = picker.predict(torch.from_numpy(X).cuda()).cpu().numpy()
         ms = np.asarray([t[-1] for t in r["trials"]])
         k = int(np.argmin(pred))
-        heur = [t[-1] for t in r["trials"] if t[:6] == r["heuristic"]]
+        heur = [t[-1] for t in r["trials"]
+                if t[:6] == r["heuristic"] and trial_sigma(t) == 2.0]
         if not heur:
             continue
         tot["picker"] += float(ms[k])
         tot["heuristic"] += float(heur[0])
         tot["best"] += float(ms.min())
         per.append(dict(seed=r["seed"], picker=float(ms[k]), heuristic=float(heur[0]),
-                        best=float(ms.min()), choice=r["trials"][k][:6]))
+                        best=float(ms.min()), choice=r["trials"][k][:6],
+                        sigma=trial_sigma(r["trials"][k])))
     tot["problems"] = len(per)
+    tot["picked_sigma125"] = sum(1 for q in per if q["sigma"] != 2.0)
     tot["regret"] = tot["picker"] / tot["best"] - 1.0 if tot["best"] > 0 else None
     tot["speedup_vs_heuristic"] = tot["heuristic"] / tot["picker"] if tot["picker"] > 0 else None
     return tot, per
@@ -205,6 +246,7 @@ def main(argv=None):
     a.add_argument("--count", type=int, default=200)
     a.add_argument("--first-seed", type=int, default=0)
     a.add_argument("--reps", type=int, default=2)
+    a.add_argument("--seconds", type=float, default=None)
     a.add_argument("--out", default=DEFAULT_TRIALS)
     a = sub.add_parser("train")
     a.add_argument("--data", default=DEFAULT_TRIALS)
@@ -220,7 +262,8 @@ def main(argv=None):
     from . import binding
     if args.cmd == "collect":
         probs = sample_problems(args.count, args.first_seed)
-        collect(probs, reps=args.reps, out=args.out, log=lambda s: print(s, flush=True))
+        collect(probs, reps=args.reps, out=args.out, log=lambda s: print(s, flush=True),
+                seconds=args.seconds)
     elif args.cmd == "train":
         rows = load_rows(args.data)
         t0 = time.time()

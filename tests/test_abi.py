@@ -119,3 +119,43 @@ def test_picker_features_without_gpu(lib):
         nb.picker_features(1, (64, 64), 1e-5, 100, 0.0, "auto")
     with pytest.raises(nb.NufftError):
         nb.picker_features(1, (64, 64), 1e-9, 100, 0.0, "sm", prec=0)
+
+
+def test_sigma_candidates_and_pick_without_gpu(lib):
+    import math
+    from paper_2102_08463_gb300 import binding as nb
+    from paper_2102_08463_gb300 import picker
+    lib = nb.load()
+    # sigma = 1.25 at eps 1e-3: w = ceil(3 / 0.6) + 1 = 6, n = next235(1.25 * 1024) = 1280
+    f = nb.picker_features(1, (1024, 1024), 1e-3, 1280 * 1280, 0.0, "sm", upsampfac=1.25)
+    assert f[3] == pytest.approx(6 / 16)
+    assert f[4] == pytest.approx(math.log2(1280 * 1280) / 32, abs=1e-7)
+    assert f[5] == pytest.approx(0.0, abs=1e-7)
+    # the sigma = 1.25 plan exists in single precision for eps >= 1e-4 only, and in
+    # double precision while w <= 16 (w = ceil(log10(1/eps) / 0.6) + 1)
+    assert picker.sigma125_width(1, (64, 64), 1e-3, 100, 0) == 6
+    assert picker.sigma125_width(1, (64, 64), 1e-5, 100, 0) is None
+    assert picker.sigma125_width(2, (64, 64, 64), 1e-9, 100, 1) == 16
+    assert picker.sigma125_width(2, (64, 64), 1e-11, 100, 1) is None
+    assert picker.trial_sigma([3, 8, 8, 1, 256, 128, 1.0]) == 2.0
+    assert picker.trial_sigma([3, 8, 8, 1, 256, 128, 1.25, 1.0]) == 1.25
+    # nufft_pick: argument errors and an eps no sigma reaches leave opts as given,
+    # and with no picker installed the answer is sigma = 2 with automatic tiles --
+    # none of these touch the device
+    arr = (ctypes.c_int64 * 3)(64, 64, 1)
+    o = nb.default_opts()
+    o.msub = 77
+    assert lib.nufft_pick(4, 2, arr, 1e-3, 0, 0, None, None, None, None, ctypes.byref(o)) \
+        == nb.NUFFT_ERR_ARG
+    assert lib.nufft_pick(1, 2, arr, 1e-3, -1, 0, None, None, None, None, ctypes.byref(o)) \
+        == nb.NUFFT_ERR_ARG
+    assert lib.nufft_pick(1, 2, arr, 1e-3, 0, 5, None, None, None, None, ctypes.byref(o)) \
+        == nb.NUFFT_ERR_ARG
+    assert lib.nufft_pick(1, 2, arr, 1e-7, 0, 0, None, None, None, None, ctypes.byref(o)) \
+        == nb.NUFFT_ERR_EPS
+    assert o.msub == 77
+    nb.Picker.uninstall()
+    assert lib.nufft_pick(1, 2, arr, 1e-3, 0, 0, None, None, None, None, ctypes.byref(o)) == 0
+    assert (o.upsampfac, o.method, tuple(o.bin), o.msub, o.threads) == (2.0, 0, (0, 0, 0), 0, 0)
+    assert lib.nufft_pick(2, 2, arr, 1e-11, 1, 0, None, None, None, None, ctypes.byref(o)) == 0
+    assert o.upsampfac == 2.0

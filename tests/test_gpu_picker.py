@@ -254,3 +254,55 @@ def test_trained_picker_gains_over_the_heuristic(nb):
     assert tot["picker"] < 0.9 * tot["heuristic"], tot
     assert tot["regret"] < 0.5, tot
     p.close()
+
+
+@pytest.mark.parametrize("type_,N", [(1, (60, 52)), (2, (24, 20, 18))])
+def test_pick_chooses_sigma_from_the_picker(nb, type_, N):
+    """nufft_pick ranks the tile candidates of both upsampling factors: a network
+    that predicts log2(n_tot) / 32 takes sigma = 1.25's smaller grid, one that
+    predicts w / 16 takes sigma = 2's narrower kernel; a plan made from the pick
+    has that factor's grid and meets the exact-sum bar."""
+    import oracle
+    dim, M, eps = len(N), 20000, 1e-3
+    pts_np = wl.points("rand", dim, M, 820 + dim, np.float32)
+    p64 = [a.astype(np.float64) for a in pts_np]
+    pts = [torch.from_numpy(a).cuda() for a in pts_np]
+    nb.Picker.uninstall()
+    assert nb.pick(type_, N, eps, *pts) == dict(upsampfac=2.0, prec=0, method="auto", bins=None,
+                                                msub=0, threads=0)
+    grid = nb.Picker(params=_one_unit_net(4, 1.0))
+    width = nb.Picker(params=_one_unit_net(3, 1.0))
+    try:
+        width.install()
+        kw = nb.pick(type_, N, eps, *pts)
+        assert kw["upsampfac"] == 2.0 and kw["method"] == "sm"
+        grid.install()
+        # single precision below 1e-4: sigma = 1.25 is no candidate
+        assert nb.pick(type_, N, 1e-5, *pts)["upsampfac"] == 2.0
+        with pytest.raises(nb.NufftError):
+            nb.pick(type_, N, 1e-7, *pts)
+        kw = nb.pick(type_, N, eps, *pts)
+        # ties within sigma = 1.25: the first candidate (SM, smallest bins, M_sub 256, 128 threads)
+        assert kw == dict(upsampfac=1.25, prec=0, method="sm",
+                          bins=(8, 8) if dim == 2 else (8, 8, 4), msub=256, threads=128)
+        with nb.Plan(type_, N, eps, **kw) as p:
+            assert tuple(p.params["nf"][:dim]) == oracle.Params(N, eps, 1.25).n
+            p.setpts(*pts)
+            if type_ == 1:
+                c = wl.strengths(M, 830, np.complex64)
+                got = p.execute(c=torch.from_numpy(c).cuda()).cpu().numpy()
+                c = c.astype(np.complex128)
+                same = oracle.nufft_type1(p64, c, N, w=p.params["w"], sigma=1.25)
+                exact = oracle.direct_type1(p64, c, N)
+            else:
+                f = wl.modes(N, 831, np.complex64)
+                got = p.execute(f=torch.from_numpy(f).cuda()).cpu().numpy()
+                f = f.astype(np.complex128)
+                same = oracle.nufft_type2(p64, f, w=p.params["w"], sigma=1.25)
+                exact = oracle.direct_type2(p64, f)
+        assert _rel(got, same) < 1e-4
+        assert oracle.rel_l2(got, exact) <= 2 * eps
+    finally:
+        nb.Picker.uninstall()
+        grid.close()
+        width.close()
