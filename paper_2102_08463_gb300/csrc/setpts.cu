@@ -368,11 +368,19 @@ bin_offsets_kernel(const int32_t *__restrict__ bincount, const int2 *__restrict_
 //     the lanes take them in lane order.  Chunks claim in order (__syncwarp
 //     between them) and warps take turns in warp order (one barrier per warp
 //     per tile), so equal keys keep their index order.
+//   kFilter (with kOrdered): match costs about one step per distinct key of
+//     the chunk, and uniform points over many bins give 32 distinct keys.  So
+//     each warp first hashes its keys into 256 byte buckets of its own (512
+//     bytes of shared memory after the bin table: bucket owner, collision
+//     mark): a lane alone in its bucket holds a key no other lane holds and is
+//     its own group; only lanes in shared buckets (equal keys or hash
+//     collisions) run match among themselves.
 //   otherwise: every point claims its own slot with a shared atomicAdd, no
 //     turns; a CTA's points of one bin fill its run of slots in atomic order.
 constexpr int kRankU = 4;
+constexpr size_t kFilterBytes = (size_t)(kCountThreads / 32) * 512;
 
-template <bool kOrdered>
+template <bool kOrdered, bool kFilter = false>
 __global__ void __launch_bounds__(kCountThreads)
 rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restrict__ keys,
                     const int32_t *__restrict__ mat, const int32_t *__restrict__ binstart,
@@ -382,8 +390,12 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int32_t *col = mat + (int64_t)blockIdx.x * nbins;
+    uint8_t *owner = reinterpret_cast<uint8_t *>(run + nbins) + warp * 512;
+    uint8_t *clash = owner + 256;
 #pragma unroll 4
     for (int i = threadIdx.x; i < nbins; i += blockDim.x) run[i] = col[i] + binstart[i];
+    if (kFilter)
+        for (int i = lane; i < 256; i += 32) clash[i] = 0;
     __syncthreads();
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = min(beg + chunk, M);
@@ -407,8 +419,23 @@ rank_scatter_kernel(int64_t M, int64_t chunk, int nbins, const int32_t *__restri
             int base[kRankU];
 #pragma unroll
             for (int u = 0; u < kRankU; ++u) {
-                peers[u] = __match_any_sync(kFull, key[u]);
                 base[u] = 0;
+                if (kFilter) {
+                    const unsigned h = ((unsigned)key[u] * 2654435761u) >> 24;   // 0..255
+                    owner[h] = (uint8_t)lane;
+                    __syncwarp();
+                    const bool lost = owner[h] != (uint8_t)lane;
+                    if (lost) clash[h] = 1;
+                    __syncwarp();
+                    const bool shared_bucket = clash[h] != 0;
+                    __syncwarp();
+                    if (lost) clash[h] = 0;                // the marks are clear again
+                    __syncwarp();
+                    const unsigned sm = __ballot_sync(kFull, shared_bucket);
+                    peers[u] = shared_bucket ? __match_any_sync(sm, key[u]) : (1u << lane);
+                } else {
+                    peers[u] = __match_any_sync(kFull, key[u]);
+                }
             }
             for (int wv = 0; wv < nwarps; ++wv) {
                 if (warp == wv) {
@@ -823,7 +850,9 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
         const int64_t chunk = (M + cblk - 1) / cblk;
         const size_t smem = (size_t)nbins * sizeof(int32_t);
         auto kc = p.dim == 1 ? count_kernel<T, 1> : p.dim == 2 ? count_kernel<T, 2> : count_kernel<T, 3>;
-        auto ks = p.unordered_bins ? rank_scatter_kernel<false> : rank_scatter_kernel<true>;
+        const bool filter = !p.unordered_bins && smem + kFilterBytes <= (size_t)p.smem_optin;
+        auto ks = p.unordered_bins ? rank_scatter_kernel<false>
+                                   : filter ? rank_scatter_kernel<true, true> : rank_scatter_kernel<true>;
         e = allow_max_smem((const void *)kc);
         if (e == cudaSuccess) e = allow_max_smem((const void *)ks);
         if (e != cudaSuccess) return e;
@@ -834,7 +863,8 @@ cudaError_t setpts_impl(Plan &p, const T *x, const T *y, const T *z)
                                                                          p.bincount, p.msub, agg);
         bin_offsets_kernel<<<(nbins + kOffThreads - 1) / kOffThreads, kOffThreads, 0, st>>>(
             p.bincount, agg, nbins, p.msub, p.binstart, p.subprob, p.nsub);
-        ks<<<cblk, kCountThreads, smem, st>>>(M, chunk, nbins, p.keys, p.mat, p.binstart, p.vals);
+        ks<<<cblk, kCountThreads, smem + (filter ? kFilterBytes : 0), st>>>(M, chunk, nbins, p.keys,
+                                                                           p.mat, p.binstart, p.vals);
         p.perm = p.vals;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
