@@ -1,6 +1,7 @@
 """Host side of the learned tile picker (no GPU): the problem sampler keeps
 its stated ranges, work bound and 80/20 split by seed, and a trial row turns
-into one 12-feature row and a log2(ms) target per candidate."""
+into one 12-feature row and a log2(ms) target per candidate, a trial timed at
+sigma = 1.25 through that factor's kernel width and grid size."""
 import math
 
 import numpy as np
@@ -63,3 +64,24 @@ def test_trial_row_features(pk):
     assert X[1, 11] == pytest.approx(128 / 256)
     # problem features are shared by every candidate
     assert np.all(X[:, :7] == X[0, :7])
+
+
+def test_trials_at_both_sigmas(pk):
+    # N = (200, 120) at eps 1e-3: sigma = 2 gives w = 4 on a 400 x 240 grid, sigma = 1.25 gives
+    # w = ceil(3 / 0.6) + 1 = 6 on 250 x 150 (both 2^a 3^b 5^c already)
+    row = dict(seed=5, type=2, dim=2, N=[200, 120], M=80000, kind="gauss", spread=0.2, eps=1e-3,
+               prec=0, w=4, skew=1.0, heuristic=[3, 12, 16, 1, 1024, 256],
+               trials=[[3, 12, 16, 1, 1024, 256, 2.0, 0.5], [3, 12, 16, 1, 1024, 256, 1.25, 0.25],
+                       [3, 8, 8, 1, 256, 128, 0.125]])
+    X, T = pk.features(row)
+    assert np.allclose(T, [-1.0, -2.0, -3.0])
+    assert [pk.trial_sigma(t) for t in row["trials"]] == [2.0, 1.25, 2.0]
+    assert X[0, 3] == pytest.approx(4 / 16) and X[2, 3] == pytest.approx(4 / 16)
+    assert X[1, 3] == pytest.approx(6 / 16)
+    assert X[0, 4] == pytest.approx(math.log2(400 * 240) / 32, abs=1e-7)
+    assert X[1, 4] == pytest.approx(math.log2(250 * 150) / 32, abs=1e-7)
+    assert X[1, 5] == pytest.approx(math.log2(80000 / (250 * 150)) / 8, abs=1e-7)
+    # the tiling features do not depend on sigma
+    assert np.all(X[0, 6:] == X[1, 6:])
+    # a problem whose sigma = 1.25 plan cannot reach eps in single precision gets no such trials
+    assert pk.sigma125_width(2, [200, 120], 1e-5, 80000, 0) is None
